@@ -1,0 +1,139 @@
+"""Pins of the oracle's pressure operator and geometric multigrid solve
+(density-weighted projection; the paper names no solver, the reading is
+red-black Gauss-Seidel V(2,2) cycles with a CG coarse solve)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+import torch
+
+import cases
+from oracle import fvm_oracle as O
+
+
+def _sphere_alpha(p, R=0.3):
+    x, y, z = cases.cell_centres(p)
+    L = p.nx * p.h
+    d = np.sqrt((x - 0.5 * L) ** 2 + (y - 0.5 * L) ** 2 + (z - 0.5 * L) ** 2)
+    return torch.tensor(np.broadcast_to((d < R * L).astype(np.float64), p.shape).copy())
+
+
+def _level(p, alpha):
+    grid = O.Grid(p)
+    return O.Level(grid.n, (grid.h,) * 3, grid.bc, O.fine_beta(alpha, p, grid)), grid
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1), (0, 0, 1), (0, 0, 0)])
+def test_operator_properties(bc):
+    """L 1 = 0, sum(L p) = 0, L symmetric and positive semi-definite."""
+    p = cases.Params(nx=8, ny=6, nz=4, h=0.1, bc=bc, rho=(1.0, 50.0))
+    alpha = torch.tensor(cases.uniform(5, p.shape, 0, 1))
+    lev, _ = _level(p, alpha)
+    one = torch.ones(p.shape, dtype=torch.float64)
+    assert O.apply_L(one, lev).abs().max().item() < 1e-12
+    x = torch.tensor(cases.uniform(6, p.shape, -1, 1))
+    y = torch.tensor(cases.uniform(7, p.shape, -1, 1))
+    Lx, Ly = O.apply_L(x, lev), O.apply_L(y, lev)
+    assert abs(Lx.sum().item()) < 1e-10
+    assert abs((x * Ly).sum().item() - (Lx * y).sum().item()) < 1e-11 * (x * Lx).sum().item()
+    assert (x * Lx).sum().item() > 0
+
+
+def test_manufactured_solution_second_order():
+    """-div grad p = f with p = cos(pi x) cos(2 pi y) cos(pi z) on the unit
+    cube with Neumann walls: the discrete solution converges at order 2."""
+    errs = []
+    for n in (8, 16, 32):
+        p = cases.Params(nx=n, ny=n, nz=n, h=1.0 / n, bc=(1, 1, 1), rho=(1.0, 1.0),
+                         mg_rtol=1e-12)
+        x, y, z = cases.cell_centres(p)
+        pex = np.cos(math.pi * x) * np.cos(2 * math.pi * y) * np.cos(math.pi * z)
+        f = (math.pi ** 2) * (1 + 4 + 1) * pex
+        f = np.broadcast_to(f, p.shape).copy()
+        sol, cyc, rel = O.poisson_solve(np.zeros(p.shape), f, np.zeros(p.shape), p)
+        assert rel <= 1e-12
+        pe = np.broadcast_to(pex, p.shape)
+        pe = pe - pe.mean()
+        errs.append(np.abs(sol.numpy() - pe).max())
+    r = [math.log(errs[i] / errs[i + 1], 2) for i in range(2)]
+    assert min(r) > 1.8, (errs, r)
+
+
+def _dense_matrix(lev, n):
+    cols = []
+    for c in range(n):
+        e = torch.zeros(n, dtype=torch.float64)
+        e[c] = 1.0
+        cols.append(O.apply_L(e.reshape(lev.shape), lev).reshape(-1).numpy())
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("ratio", [10.0, 100.0, 7900.0])
+def test_against_direct_sparse_solve(ratio):
+    """Multigrid to 1e-12 agrees with scipy's direct sparse solve of the same
+    (gauge-fixed) system for sharp density jumps."""
+    p = cases.Params(nx=16, ny=16, nz=16, h=1.0 / 16, bc=(1, 0, 1), rho=(1.0, ratio),
+                     mg_rtol=1e-12, mg_max_cycles=400)
+    alpha = _sphere_alpha(p)
+    lev, grid = _level(p, alpha)
+    N = p.ncells
+    A = _dense_matrix(lev, N)
+    b = cases.uniform(11, (N,), -1, 1)
+    b = b - b.mean()
+    # gauge: replace the last equation by sum(p) = 0
+    A2 = A.copy()
+    A2[-1, :] = 1.0
+    b2 = b.copy()
+    b2[-1] = 0.0
+    xd = spla.spsolve(sp.csr_matrix(A2), b2)
+    xm, cyc, rel = O.poisson_solve(alpha, b.reshape(p.shape), np.zeros(p.shape), p)
+    assert rel <= 1e-12, (cyc, rel)
+    err = np.abs(xm.numpy().reshape(-1) - xd).max() / np.abs(xd).max()
+    assert err < 1e-9, err
+
+
+def test_vcycle_is_symmetric():
+    """The V-cycle with red-black pre- and black-red post-smoothing is a
+    symmetric operator b -> x (from x0 = 0)."""
+    p = cases.Params(nx=16, ny=16, nz=8, h=1.0 / 16, bc=(1, 0, 1), rho=(1.0, 30.0),
+                     coarse_rtol=1e-14)
+    alpha = _sphere_alpha(p)
+    grid = O.Grid(p)
+    levels = O.build_hierarchy(O.fine_beta(alpha, p, grid), grid, p.mg_levels)
+    y = torch.tensor(cases.uniform(21, p.shape, -1, 1))
+    z = torch.tensor(cases.uniform(22, p.shape, -1, 1))
+    y, z = y - y.mean(), z - z.mean()
+    My = O.vcycle(levels, 0, torch.zeros_like(y), y, p)
+    Mz = O.vcycle(levels, 0, torch.zeros_like(z), z, p)
+    a, b = (z * My).sum().item(), (y * Mz).sum().item()
+    assert abs(a - b) <= 1e-11 * abs(a)
+
+
+def test_hierarchy_rules():
+    p = cases.Params(nx=128, ny=128, nz=64, h=1.0, bc=(0, 0, 1))
+    grid = O.Grid(p)
+    beta = [torch.ones(p.shape, dtype=torch.float64)] * 3
+    levels = O.build_hierarchy(beta, grid, 16)
+    sizes = [lev.n for lev in levels]
+    assert sizes[0] == (128, 128, 64)
+    assert sizes[-1] == (2, 2, 2)
+    for lev in levels:
+        for d in range(3):
+            if lev.bc[d] == O.PERIODIC and lev.n[d] > 1:
+                assert lev.n[d] % 2 == 0
+    # coarse beta of a constant field stays constant (mean of covered faces)
+    assert all(torch.allclose(b, torch.ones_like(b)) for b in levels[2].beta[:2])
+
+
+def test_convergence_factor_reasonable():
+    """A V(2,2) cycle reduces the residual by at least 4x per cycle on a
+    density ratio of 100."""
+    p = cases.Params(nx=32, ny=32, nz=32, h=1.0 / 32, bc=(1, 1, 1), rho=(1.0, 100.0),
+                     mg_rtol=1e-10)
+    alpha = _sphere_alpha(p)
+    b = cases.uniform(31, p.shape, -1, 1)
+    x, cyc, rel = O.poisson_solve(alpha, b, np.zeros(p.shape), p)
+    assert rel <= 1e-10
+    assert cyc <= 17
