@@ -1,0 +1,392 @@
+"""Throughput of the thermocapillary two-phase step on GB300.
+
+Workload: the 256^3 melt-pool surrogate (liquid rho 7900 under gas rho 1,
+dsigma/dT = -4.3e-4 N/(m K), moving Gaussian surface heat flux, seeded 1 %
+temperature perturbation), mixed-precision step (float transport, double
+projection refinement to ||r|| <= 1e-10 ||b||), dt from the stability limits.
+A step is one full SSP-RK3 step: three stages, three projections.
+
+Metric: cell-updates per second = cells / step time (whole job: summed over
+ranks; with more than one GPU each rank runs an independent replica).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line is printed by rank 0.  ``--impl reference`` times the CPU
+oracle on the host cores (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per full step at 256^3 (FP64 vs mixed) & HBM roofline %"
+UNIT = "cell-updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM = 6800.0
+
+# algorithmic bytes per cell of one launch of a fine-level kernel class, for
+# element size s (4 mixed, 8 double) and beta size bs; the derivation of each
+# figure is in the design notes (every array a kernel must touch, streamed once)
+def alg_bytes_per_cell(cls: str, mixed: bool) -> float | None:
+    s = 4 if mixed else 8
+    bs = s
+    table = {
+        "gs_fine": 2 * s + s + 3 * bs,          # x read+write, b, three face betas
+        "momentum": 9 * s + 3 * s,               # u,v,w,alpha,T,kappa,M0..2 in; u*,v*,w* out
+        "scalars": 7 * s + 2 * s,                # u,v,w,alpha,T,Sn alpha,Sn T in; alpha,T out
+        "interface": 3 * s + 4 * s,              # alpha, smoothed alpha, T in; kappa, M out
+        "smooth": 2 * s,
+        "div_rhs": 3 * s + 8,
+        "correct": 6 * s + 8 + 3 * bs + 3 * s,   # u*, Sn u, p, beta in; u out
+        "residual64": 8 + 8 + 3 * 4 + 4,         # p, b, float beta in; float r out
+        "add_correction": 8 + 4 + 8,
+        "restrict_fine": 2 * s + s + 3 * bs + 2 * s / 8,
+        "prolong_fine": 2 * s + s / 8,
+        "resnorm": 2 * s + 3 * bs,
+        "beta": s + 3 * bs,
+    }
+    return table.get(cls)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cells per axis (default 256)")
+    ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2209_09671_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(cls: str, mixed: bool):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernels changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    key = f"{cls}/{'mixed' if mixed else 'f64'}"
+    v = d.get("per_launch_bytes", {}).get(key)
+    return float(v) if v is not None else None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if len(s) >= 8 and s[0].replace(".", "").isdigit()]
+        smax = [float(s[1]) for s in self.samples if len(s) >= 8 and s[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for s in self.samples:
+            if len(s) < 8:
+                continue
+            for k, name in enumerate(names):
+                if s[4 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def cpu_oracle_sample(target_s: float = 15.0):
+    """The FP64 oracle on the host cores: melt-pool recipe (same h, physics and
+    seed) at 48^3, as many steps as fit in about target_s seconds (>= 1)."""
+    import torch
+
+    import cases
+    from oracle import fvm_oracle as O
+    n = 48
+    p, s = cases.melt_pool(n, n, n, precision=cases.F64)
+    t0 = time.perf_counter()
+    st = s
+    steps = 0
+    while True:
+        st, _ = O.step(st, p, steps, 0.0)
+        steps += 1
+        if time.perf_counter() - t0 >= target_s or steps >= 8:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle, melt-pool recipe at {n}^3 (h, physics, seed of the 256^3 "
+                      f"workload), {steps} full steps in {el:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_oracle_sample(target_s=20.0)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": None, "warmup": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "melt-pool surrogate (CPU oracle sample, 48^3 of the "
+                                   "256^3 recipe)", "grid": [48, 48, 48]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def make_workload(n, precision):
+    import cases
+    p, s = cases.melt_pool(n, n, n, precision=precision)
+    return p, s
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import cases
+    import paper_2209_09671_gb300 as P
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    N = n ** 3
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return t.item()
+
+    # ---------------- mixed-precision step (the headline) -------------------
+    p, s0 = make_workload(n, cases.MIXED)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        solver = P.Solver(p, device=dev, stream=stream)
+        state = P.to_device(s0, True, dev)
+    step_idx = 0
+    for _ in range(args.warmup):
+        solver.fvm_step(state, step_idx, 0.0, info=False)
+        step_idx += 1
+    stream.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    solver.fvm_profile(True)
+    solver.fvm_launch_count(reset=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        solver.fvm_step(state, step_idx, 0.0, info=False)
+        step_idx += 1
+    ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = solver.fvm_launch_count()
+    prof = solver.fvm_profile_read()
+    solver.fvm_profile(False)
+    clk = clocks.stop()
+    info = solver.fvm_step(state, step_idx, 0.0, info=True)   # untimed: state sanity
+    step_idx += 1
+    t_step = max_over_ranks(elapsed / args.steps)
+    value = world * N / t_step
+
+    # dominant kernel and its roofline
+    peak, peak_kind = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    cls, (nl, ms) = dom
+    bpc = alg_bytes_per_cell(cls, True)
+    roof = None
+    if bpc is not None and nl > 0:
+        per_launch_s = ms / 1e3 / nl
+        bytes_launch = bpc * N
+        achieved = bytes_launch / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel": cls, "achieved": achieved, "peak": peak,
+                "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_for(cls, True),
+                "alg_bytes_per_launch": bytes_launch, "launches": nl,
+                "mean_launch_us": per_launch_s * 1e6,
+                "share_of_step": ms / 1e3 / elapsed}
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / 1e3 / elapsed, 4)}
+               for k, v in prof.items() if v[0]}
+
+    # ---------------- end to end through host buffers -------------------------
+    host = {k: v.to("cpu").pin_memory() for k, v in state.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = h2d
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            for k in state:
+                state[k].copy_(host[k], non_blocking=True)
+            solver.fvm_step(state, step_idx, 0.0, info=False)
+            for k in state:
+                host[k].copy_(state[k], non_blocking=True)
+            step_idx += 1
+    stream.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            for k in state:
+                state[k].copy_(host[k], non_blocking=True)
+            solver.fvm_step(state, step_idx, 0.0, info=False)
+            for k in state:
+                host[k].copy_(state[k], non_blocking=True)
+            step_idx += 1
+    e1.record(stream)
+    stream.synchronize()
+    barrier()
+    e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3 / e2e_steps)
+    solver.close()
+    del state, host, solver
+    torch.cuda.empty_cache()
+
+    # ---------------- FP64 step (side measurement, same workload) ----------
+    f64 = None
+    if args.f64_steps > 0:
+        p64, s64 = make_workload(n, cases.F64)
+        with torch.cuda.stream(stream):
+            sol64 = P.Solver(p64, device=dev, stream=stream)
+            st64 = P.to_device(s64, False, dev)
+        sol64.fvm_step(st64, 0, 0.0, info=False)
+        stream.synchronize()
+        sol64.fvm_profile(True)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for q in range(args.f64_steps):
+            sol64.fvm_step(st64, 1 + q, 0.0, info=False)
+        a1.record(stream)
+        stream.synchronize()
+        t64 = max_over_ranks(a0.elapsed_time(a1) / 1e3 / args.f64_steps)
+        prof64 = sol64.fvm_profile_read()
+        inf64 = sol64.fvm_step(st64, 1 + args.f64_steps, 0.0, info=True)
+        f64 = {"value": world * N / t64, "ms_per_step": t64 * 1e3, "steps": args.f64_steps,
+               "vcycles_last_step": inf64["vcycles"],
+               "kernels_ms": {k: round(v[1], 2) for k, v in prof64.items() if v[0]},
+               "bound": "alu (FP64 units)"}
+        sol64.close()
+        del st64, sol64
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu else cpu_oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 transport + f64 projection",
+        "data": "synthetic",
+        "config": {"workload": f"melt-pool surrogate {n}^3 (rho 7900/1, mixed precision)",
+                   "grid": [n, n, n], "precision": "mixed", "mg_rtol": p.mg_rtol,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (state 448 MB)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * N / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "f64": f64,
+        "last_step_info": info,
+        "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

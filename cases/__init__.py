@@ -217,14 +217,15 @@ def thermocapillary_channel(nx: int = 128, ny: int = 128, nz: int = 64, dT: floa
 
 
 def melt_pool(nx: int = 256, ny: int = 256, nz: int = 256, h: float = 2e-6,
-              seed: int = SEED, q_power: float = 10.0, precision: int = MIXED):
+              seed: int = SEED, q_power: float = 5e-3, precision: int = MIXED,
+              noise_corr_cells: float = 8.0):
     """Melt-pool surrogate (256^3 by default, h = 2 um).
 
     Periodic x, y; walls in z (adiabatic).  Liquid 316L-like layer
     (alpha = 1) below z = nz/2 cells: rho 7900, mu 5.85e-3, cp 790,
     lambda 6.6; gas above: rho 1, mu 5.85e-5, cp 1900, lambda 0.02.
-    sigma0 1.908 N/m, dsigma/dT = -4.3e-4 N/(m K), T0 = 1700 K with seeded
-    1 % uniform noise.  Gaussian surface heat flux of radius 8 cells starting
+    sigma0 1.908 N/m, dsigma/dT = -4.3e-4 N/(m K), T0 = 1700 K with a seeded
+    smooth 1 % temperature perturbation (correlation length ~8 cells).  Gaussian surface heat flux of radius 8 cells starting
     at (nx/8, ny/2) cells and moving +x by 0.5 cell per step; gravity -z.
     """
     p = Params(nx=nx, ny=ny, nz=nz, h=h, bc=(PERIODIC, PERIODIC, WALL),
@@ -236,9 +237,25 @@ def melt_pool(nx: int = 256, ny: int = 256, nz: int = 256, h: float = 2e-6,
     s = zero_state(p)
     x, y, z = cell_centres(p)
     s["alpha"][:] = np.broadcast_to((z < (nz // 2) * h).astype(np.float64), p.shape)
-    xi = uniform(seed, p.shape, -1.0, 1.0)
-    s["T"][:] = p.T0 * (1.0 + 0.01 * xi)
+    s["T"][:] = p.T0 * (1.0 + 0.01 * smooth_noise(seed, p.shape, corr_cells=noise_corr_cells))
     return p, s
+
+
+def smooth_noise(seed: int, shape, corr_cells: float = 8.0) -> np.ndarray:
+    """Seeded random field with values in [-1, 1] and a correlation length of
+    about ``corr_cells`` cells: uniform white noise low-pass filtered in
+    Fourier space by exp(-(k corr/2)^2), then scaled to max |value| = 1."""
+    xi = uniform(seed, shape, -1.0, 1.0)
+    F = np.fft.rfftn(xi)
+    ks = [np.fft.fftfreq(n) for n in shape[:-1]] + [np.fft.rfftfreq(shape[-1])]
+    K2 = np.zeros(F.shape)
+    for ax, k in enumerate(ks):
+        sh = [1] * len(shape)
+        sh[ax] = k.size
+        K2 = K2 + (2 * math.pi * k.reshape(sh)) ** 2
+    F *= np.exp(-K2 * (corr_cells / 2.0) ** 2)
+    out = np.fft.irfftn(F, s=shape, axes=tuple(range(len(shape))))
+    return out / np.abs(out).max()
 
 
 def random_smooth_state(p: Params, seed: int = SEED, amp_u: float = 1.0,

@@ -1,0 +1,180 @@
+/*
+ * fvm.h -- C ABI of the GB300 library for one explicit time step of the
+ * thermocapillary two-phase finite-volume method of Zimbrod, Schreter &
+ * Schilp (2022): conservative phase-fraction transport (Sec. III, Eq. 1),
+ * capillary stress split into a normal CSF force and a tangential Marangoni
+ * force (Sec. III, Eq. 2-4), surface tension evaluated as a cell field and
+ * differentiated directly (Sec. III, Eq. 5; Sec. IV), high-order WENO face
+ * values (Sec. IV) and the incompressible Navier-Stokes / energy equations
+ * that Sec. III names, closed by a density-weighted pressure projection.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Grid      nx x ny x nz cubic cells of edge h.  Every field is a dense
+ *            array of nx*ny*nz elements in C order [k][j][i] (x fastest).
+ *  Faces     velocities live on cell faces (MAC layout) in "low face" form:
+ *            u[k][j][i] is the x-velocity on the face between cells i-1 and
+ *            i; likewise v on y-faces and w on z-faces.  The face at index n
+ *            is implied: 0 on a wall axis, equal to face 0 on a periodic
+ *            axis.  On a wall axis the stored face 0 is the wall; it is
+ *            ignored on input and written as 0.
+ *  Phases    alpha = 1 is the phase with index [1] of the property pairs.
+ *  Memory    all field pointers are DEVICE pointers owned by the caller.
+ *            The library never allocates device memory: the caller passes a
+ *            workspace of fvm_workspace_size() bytes to fvm_create() and
+ *            keeps it alive until fvm_destroy().  The library never frees
+ *            caller memory.
+ *  Streams   work is enqueued on the stream given to fvm_create().  A call
+ *            returns after the host has read what it needs (the residual
+ *            norm of each multigrid cycle unless mg_fixed_cycles > 0, and
+ *            the diagnostics when info != NULL); device work may still be
+ *            running otherwise.
+ *  Errors    functions return an fvm_status; no C++ exception, abort or
+ *            device trap crosses the ABI.  fvm_last_error() gives a message.
+ *  Precision FVM_F64: u, v, w, alpha, T are double.  FVM_MIXED: they are
+ *            float; the pressure p, the projection right-hand side, the
+ *            outer residual of the pressure solve, the divergence check and
+ *            the diagnostic sums stay double.
+ */
+#ifndef FVM_H
+#define FVM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FVM_OK = 0,
+  FVM_EINVAL = 1,        /* bad argument or parameter                         */
+  FVM_ENOMEM = 2,        /* workspace too small                               */
+  FVM_ECUDA = 3,         /* a CUDA runtime call failed                        */
+  FVM_ENOCONV = 4,       /* pressure solve hit mg_max_cycles above mg_rtol    */
+  FVM_EUNSTABLE = 5,     /* NaN or Inf in the state or a residual             */
+  FVM_ETIMEOUT = 6,      /* reserved: a bounded device wait ran out           */
+  FVM_EUNSUPPORTED = 7   /* valid but not implemented (see fvm_last_error)    */
+} fvm_status;
+
+typedef enum { FVM_F64 = 0, FVM_MIXED = 1 } fvm_precision;
+typedef enum { FVM_BC_PERIODIC = 0, FVM_BC_WALL = 1 } fvm_bc_kind;
+typedef enum { FVM_TBC_NEUMANN = 0, FVM_TBC_DIRICHLET = 1 } fvm_tbc_kind;
+
+/* Parameters of the discrete method.  Sides are ordered -x,+x,-y,+y,-z,+z. */
+typedef struct {
+  int nx, ny, nz;            /* cells; a wall axis needs >= 4 cells             */
+  double h;                  /* cell edge [m]                                   */
+  int bc[3];                 /* fvm_bc_kind per axis x, y, z (no-slip walls)     */
+  int tbc[6];                /* fvm_tbc_kind per side; Dirichlet on one axis max */
+  double tbc_T0[6];          /* Dirichlet wall temperature                       */
+  double tbc_dTamp[6];       /*   T_w = T0 + dTamp cos(2 pi s / L_s), s = x on   */
+                             /*   y- and z-walls, s = y on x-walls               */
+  double rho[2], mu[2], cp[2], lambda[2];  /* [0]: alpha = 0 phase, [1]: alpha = 1 */
+  double sigma0, dsigma_dT, T0;            /* sigma(T) = sigma0 + dsigma_dT (T - T0) */
+  double g[3];                             /* gravity [m/s^2]                    */
+  double q_power, q_radius, q_x0, q_y0;    /* Gaussian surface heat flux          */
+  double q_speed;                          /* centre moves q_speed*h per step in +x */
+  double cfl, c_cap, c_visc, c_therm, dt_max; /* time-step limit constants       */
+  double weno_eps, weno_scale[3];          /* WENO5 eps = weno_eps*scale^2 for    */
+                                           /* alpha, T, velocity                 */
+  int smooth_passes;                       /* [1,2,1]/4 passes for curvature      */
+  int mg_levels, mg_pre, mg_post;          /* hierarchy depth cap, V(pre,post)    */
+  int mg_max_cycles, mg_fixed_cycles;      /* fixed > 0: exactly that many cycles */
+  double mg_rtol;                          /* ||b - L p|| <= rtol ||b||           */
+  double coarse_rtol; int coarse_maxit;    /* CG on the coarsest level            */
+  int precision;                           /* fvm_precision                       */
+  int mx_inner_cycles;                     /* float V-cycles per double refinement */
+} fvm_params;
+
+/* Caller-owned device fields of one state. u, v, w, alpha, T: double (F64) or
+ * float (MIXED); p: double in both forms. */
+typedef struct {
+  void *u, *v, *w, *alpha, *T;
+  double *p;
+} fvm_state;
+
+typedef struct {
+  double dt;              /* step used                                          */
+  int dt_limiter;         /* 0 CFL, 1 capillary, 2 viscous, 3 thermal, 4 dt_max,  */
+                          /* -1 when the caller gave dt                         */
+  int vcycles[3];         /* pressure V-cycles (F64) or refinements (MIXED) per stage */
+  double rel_residual[3]; /* final ||b - L p|| / ||b|| per stage                  */
+  double max_div_dt;      /* max |D u| dt of the new velocity                   */
+  double vol_sum;         /* sum alpha h^3                                      */
+  double mass_sum;        /* sum rho(alpha) h^3                                 */
+  int nan_flag;           /* 1 if the new state holds NaN/Inf                   */
+} fvm_step_info;
+
+typedef struct fvm_ctx fvm_ctx;
+
+/* Bytes of device workspace the parameters need (host only, no CUDA call).
+ * Returns FVM_EINVAL for invalid parameters. */
+fvm_status fvm_workspace_size(const fvm_params* prm, size_t* bytes);
+
+/* Bind parameters, a caller-owned device workspace of at least
+ * fvm_workspace_size() bytes (256-byte aligned) and a cudaStream_t (NULL =
+ * legacy default stream) into a context.  The context (host memory) is owned
+ * by the library until fvm_destroy().  No device memory is allocated. */
+fvm_status fvm_create(const fvm_params* prm, void* workspace, size_t bytes,
+                      void* cuda_stream, fvm_ctx** out);
+
+fvm_status fvm_destroy(fvm_ctx* ctx);
+
+/* One SSP-RK3 step with a projection per stage (the paper's Sec. III system,
+ * time integrator and coupling as the design notes read them), in place on
+ * *st.  step_index places the moving heat source; dt <= 0 selects the
+ * minimum of the CFL, capillary, viscous and thermal limits and dt_max.
+ * info may be NULL.  Returns FVM_ENOCONV / FVM_EUNSTABLE as documented. */
+fvm_status fvm_step(fvm_ctx* ctx, fvm_state* st, long step_index, double dt,
+                    fvm_step_info* info);
+
+/* The density-weighted pressure solve alone: L p = rhs with
+ * (L p)_c = sum_faces beta_f (p_c - p_nb)/h^2, beta_f = 2/(rho_L + rho_R) from
+ * alpha (0 on wall faces).  rhs (double, device) is made mean-free on a
+ * device copy; p (double, device) is the initial guess on entry and the
+ * mean-free solution on exit.  alpha is double (F64) or float (MIXED); in
+ * MIXED form the solve is the float multigrid inside double defect
+ * correction.  info->vcycles[0] and rel_residual[0] report the solve. */
+fvm_status fvm_poisson_solve(fvm_ctx* ctx, const void* alpha, const double* rhs,
+                             double* p, fvm_step_info* info);
+
+/* Reverse-mode (adjoint) of one step: not implemented in this library yet;
+ * returns FVM_EUNSUPPORTED. */
+fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index,
+                            double dt, const fvm_state* lam_np1, fvm_state* lam_n,
+                            double dtheta[2]);
+
+/* ---- measurement aid (no counterpart in the paper) ----------------------
+ * Kernel classes timed with CUDA events on the context's stream while
+ * profiling is on.  fvm_profile(ctx, 1) creates the events on first use
+ * (driver objects, no device memory from the workspace) and zeroes the
+ * totals; fvm_profile(ctx, 0) stops recording.  fvm_profile_read()
+ * synchronises the stream and returns the launches and total milliseconds of
+ * one class since the last fvm_profile(ctx, 1).  Timing adds two event
+ * records per launch. */
+typedef enum {
+  FVM_K_SMOOTH = 0, FVM_K_INTERFACE, FVM_K_SCALARS, FVM_K_MOMENTUM, FVM_K_DIV_RHS,
+  FVM_K_BETA, FVM_K_GS_FINE, FVM_K_GS_COARSE, FVM_K_RESTRICT_FINE, FVM_K_RESTRICT_COARSE,
+  FVM_K_PROLONG_FINE, FVM_K_PROLONG_COARSE, FVM_K_COARSE_CG, FVM_K_RESNORM,
+  FVM_K_RESIDUAL64, FVM_K_ADD_CORRECTION, FVM_K_CORRECT, FVM_K_DT, FVM_K_DIAGNOSTICS,
+  FVM_K_MISC, FVM_KCLASS_COUNT
+} fvm_kernel_class;
+
+fvm_status fvm_profile(fvm_ctx* ctx, int on);
+fvm_status fvm_profile_read(fvm_ctx* ctx, int kernel_class, long* launches, double* total_ms);
+
+/* Number of CUDA kernels the context has launched (counted always, host
+ * side); reset != 0 zeroes the counter after reading it. */
+fvm_status fvm_launch_count(fvm_ctx* ctx, int reset, long* count);
+
+const char* fvm_status_string(fvm_status s);
+const char* fvm_last_error(const fvm_ctx* ctx);
+
+/* Library version string. */
+const char* fvm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVM_H */

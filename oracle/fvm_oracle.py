@@ -650,7 +650,8 @@ def gs_colour(p, b, lev, colour):
 
 def coarse_cg(b, lev, rtol, maxit):
     """Conjugate gradients on the coarsest level, mean-removed right-hand
-    side, x0 = 0, stop at ||r|| <= rtol ||b||; mean-free result."""
+    side, x0 = 0, stop at ||r|| <= rtol ||b|| or on breakdown (p.Ap <= 0);
+    mean-free result."""
     b = b - b.mean()
     bn = torch.sqrt((b * b).sum())
     x = torch.zeros_like(b)
@@ -663,7 +664,10 @@ def coarse_cg(b, lev, rtol, maxit):
         if torch.sqrt(rr).item() <= rtol * bn.item():
             break
         Ad = apply_L(d, lev)
-        a = rr / (d * Ad).sum()
+        pAp = (d * Ad).sum()
+        if not pAp.item() > 0.0:   # breakdown: the search direction carries no energy
+            break
+        a = rr / pAp
         x = x + a * d
         r = r - a * Ad
         rr_new = (r * r).sum()
@@ -825,6 +829,10 @@ def step(state, prm, step_index=0, dt=0.0, fixed_cycles=None):
     """
     grid = Grid(prm)
     Sn = {k: _t(v) for k, v in state.items()}
+    # the stored wall faces are not part of the state: they are read as 0
+    for d, k in enumerate(("u", "v", "w")):
+        if grid.bc[d] == WALL:
+            Sn[k] = _zero_wall_face(Sn[k], d)
     limiter = -1
     if dt <= 0.0:
         dt, limiter = time_step_limit(Sn, prm, grid)

@@ -1,0 +1,773 @@
+// C ABI and host runtime of libfvm: parameter checks, workspace plan,
+// multigrid hierarchy, the SSP-RK3 stage sequence and the pressure solvers.
+// All device memory comes from the caller's workspace; the context itself
+// lives in host memory.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "fvm_internal.h"
+
+using namespace fvm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Plan {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + kAlign - 1) / kAlign * kAlign;
+    return o;
+  }
+};
+
+struct LevelShape {
+  int n[3];
+  double hd[3];
+  int f[3];
+};
+
+int build_levels(const fvm_params& p, LevelShape* lv) {
+  int nl = 0;
+  LevelShape cur;
+  cur.n[0] = p.nx; cur.n[1] = p.ny; cur.n[2] = p.nz;
+  for (int d = 0; d < 3; ++d) { cur.hd[d] = p.h; cur.f[d] = 1; }
+  lv[nl++] = cur;
+  while (nl < p.mg_levels && nl < kMaxLevels) {
+    LevelShape& L = lv[nl - 1];
+    int f[3];
+    bool any = false;
+    for (int d = 0; d < 3; ++d) {
+      bool ok = L.n[d] % 2 == 0 && L.n[d] >= 4;
+      if (ok && p.bc[d] == PER && (L.n[d] / 2) % 2 != 0) ok = false;
+      f[d] = ok ? 2 : 1;
+      any = any || ok;
+    }
+    if (!any) break;
+    LevelShape nx;
+    for (int d = 0; d < 3; ++d) {
+      L.f[d] = f[d];
+      nx.n[d] = L.n[d] / f[d];
+      nx.hd[d] = L.hd[d] * f[d];
+      nx.f[d] = 1;
+    }
+    lv[nl++] = nx;
+  }
+  return nl;
+}
+
+Geo make_geo(const fvm_params& p, const LevelShape& s) {
+  Geo g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = s.n[d];
+    g.bc[d] = p.bc[d];
+    g.hd[d] = s.hd[d];
+  }
+  g.h = p.h;
+  g.sy = g.n[0];
+  g.sz = (long long)g.n[0] * g.n[1];
+  g.N = g.sz * g.n[2];
+  return g;
+}
+
+const char* check_params(const fvm_params* p) {
+  if (!p) return "params is NULL";
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "grid sizes must be >= 1";
+  if (!(p->h > 0.0)) return "h must be > 0";
+  int ndir = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (p->bc[d] != FVM_BC_PERIODIC && p->bc[d] != FVM_BC_WALL) return "bc must be 0 or 1";
+    int n = d == 0 ? p->nx : (d == 1 ? p->ny : p->nz);
+    if (p->bc[d] == FVM_BC_WALL && n < 4) return "a wall axis needs >= 4 cells";
+    bool dl = p->tbc[2 * d] == FVM_TBC_DIRICHLET, dh = p->tbc[2 * d + 1] == FVM_TBC_DIRICHLET;
+    if ((dl || dh) && p->bc[d] != FVM_BC_WALL) return "Dirichlet temperature needs a wall axis";
+    if (dl || dh) ++ndir;
+  }
+  if (ndir > 1) return "Dirichlet temperature on more than one axis is not supported";
+  for (int q = 0; q < 2; ++q) {
+    if (!(p->rho[q] > 0.0) || !(p->cp[q] > 0.0) || !(p->lambda[q] > 0.0) || !(p->mu[q] >= 0.0))
+      return "rho, cp, lambda must be > 0 and mu >= 0";
+  }
+  if (p->precision != FVM_F64 && p->precision != FVM_MIXED) return "precision must be 0 or 1";
+  if (p->smooth_passes < 0 || p->mg_levels < 1 || p->mg_pre < 0 || p->mg_post < 0 ||
+      p->mg_max_cycles < 1 || p->mg_fixed_cycles < 0 || p->coarse_maxit < 1 ||
+      p->mx_inner_cycles < 1)
+    return "multigrid counts out of range";
+  if (!(p->mg_rtol > 0.0) || !(p->coarse_rtol > 0.0)) return "tolerances must be > 0";
+  if (!(p->weno_eps > 0.0)) return "weno_eps must be > 0";
+  if (p->q_power != 0.0 && !(p->q_radius > 0.0)) return "q_radius must be > 0";
+  return nullptr;
+}
+
+}  // namespace
+
+struct fvm_ctx {
+  fvm_params prm;
+  Geo g;
+  Phys ph;
+  TBC tb;
+  cudaStream_t stream;
+  bool mixed;
+  size_t rsz;            // bytes of the working precision
+  char* ws;
+  size_t ws_bytes;
+  // stage buffers (working precision)
+  void* A[5];
+  void* B[5];
+  void* as;
+  void* tmp;
+  void* kappa;
+  void* M[3];
+  void* us[3];
+  double* b;             // projection right-hand side
+  void* beta0[3];        // fine beta (double in F64, float in MIXED)
+  float* e32;            // MIXED: inner correction
+  float* r32;            // MIXED: inner right-hand side
+  // hierarchy
+  int nlev;
+  LevelShape shp[kMaxLevels];
+  void* lx[kMaxLevels];
+  void* lb[kMaxLevels];
+  void* lbeta[kMaxLevels][3];
+  void* cg[3];
+  // reduction scratch
+  double* partial;
+  double* scal;          // 16 doubles
+  unsigned long long* maxbits;
+  int* flags;
+  double* dt_dev;
+  int* lim_dev;
+  // kernel timing with CUDA events (measurement aid, off by default)
+  int prof;
+  int prof_n;
+  cudaEvent_t* prof_ev;      // 2 * kProfSlots events
+  int* prof_cls;
+  long nlaunch;              // kernels launched since the last count reset
+  long prof_launches[FVM_KCLASS_COUNT];
+  double prof_ms[FVM_KCLASS_COUNT];
+  char err[512];
+};
+
+namespace {
+
+constexpr int kProfSlots = 4096;
+
+void prof_fold(fvm_ctx* c) {
+  if (!c->prof_n) return;
+  cudaStreamSynchronize(c->stream);
+  for (int q = 0; q < c->prof_n; ++q) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->prof_ev[2 * q], c->prof_ev[2 * q + 1]) == cudaSuccess) {
+      c->prof_ms[c->prof_cls[q]] += ms;
+      c->prof_launches[c->prof_cls[q]] += 1;
+    }
+  }
+  c->prof_n = 0;
+}
+
+struct ProfScope {
+  fvm_ctx* c;
+  int slot;
+  ProfScope(fvm_ctx* ctx, int cls) : c(ctx), slot(-1) {
+    if (!c->prof) return;
+    if (c->prof_n == kProfSlots) prof_fold(c);
+    slot = c->prof_n++;
+    c->prof_cls[slot] = cls;
+    cudaEventRecord(c->prof_ev[2 * slot], c->stream);
+  }
+  ~ProfScope() {
+    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], c->stream);
+  }
+};
+
+// every kernel launch of the library goes through TIMED(ctx, class, kernels, call):
+// it counts the kernels and, while profiling is on, brackets them with events
+#define TIMED(ctx, cls, nk, ...) \
+  do {                           \
+    (ctx)->nlaunch += (nk);      \
+    ProfScope _ps(ctx, cls);     \
+    __VA_ARGS__;                 \
+  } while (0)
+
+size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
+  Plan pl;
+  LevelShape lv[kMaxLevels];
+  int nl = build_levels(p, lv);
+  long long N = (long long)p.nx * p.ny * p.nz;
+  bool mixed = p.precision == FVM_MIXED;
+  size_t rs = mixed ? sizeof(float) : sizeof(double);
+  size_t ms = rs;   // multigrid precision: double in F64, float (inner) in MIXED
+  size_t o_A[5], o_B[5], o_as, o_tmp, o_k, o_M[3], o_us[3], o_b, o_beta[3], o_e = 0, o_r = 0;
+  for (int q = 0; q < 5; ++q) o_A[q] = pl.take(N * rs);
+  for (int q = 0; q < 5; ++q) o_B[q] = pl.take(N * rs);
+  o_as = pl.take(N * rs);
+  o_tmp = pl.take(N * rs);
+  o_k = pl.take(N * rs);
+  for (int q = 0; q < 3; ++q) o_M[q] = pl.take(N * rs);
+  for (int q = 0; q < 3; ++q) o_us[q] = pl.take(N * rs);
+  o_b = pl.take(N * sizeof(double));
+  for (int q = 0; q < 3; ++q) o_beta[q] = pl.take(N * ms);
+  if (mixed) {
+    o_e = pl.take(N * sizeof(float));
+    o_r = pl.take(N * sizeof(float));
+  }
+  size_t o_lx[kMaxLevels], o_lb[kMaxLevels], o_lbeta[kMaxLevels][3];
+  for (int l = 1; l < nl; ++l) {
+    long long n = (long long)lv[l].n[0] * lv[l].n[1] * lv[l].n[2];
+    o_lx[l] = pl.take(n * ms);
+    o_lb[l] = pl.take(n * ms);
+    for (int q = 0; q < 3; ++q) o_lbeta[l][q] = pl.take(n * ms);
+  }
+  long long nc = (long long)lv[nl - 1].n[0] * lv[nl - 1].n[1] * lv[nl - 1].n[2];
+  size_t o_cg[3];
+  for (int q = 0; q < 3; ++q) o_cg[q] = pl.take(nc * ms);
+  size_t o_part = pl.take(2 * kRedBlocks * sizeof(double));
+  size_t o_scal = pl.take(16 * sizeof(double));
+  size_t o_max = pl.take(8 * sizeof(unsigned long long));
+  size_t o_flags = pl.take(8 * sizeof(int));
+  size_t o_dt = pl.take(sizeof(double));
+  size_t o_lim = pl.take(sizeof(int));
+  if (c) {
+    char* w = c->ws;
+    for (int q = 0; q < 5; ++q) { c->A[q] = w + o_A[q]; c->B[q] = w + o_B[q]; }
+    c->as = w + o_as;
+    c->tmp = w + o_tmp;
+    c->kappa = w + o_k;
+    for (int q = 0; q < 3; ++q) {
+      c->M[q] = w + o_M[q];
+      c->us[q] = w + o_us[q];
+      c->beta0[q] = w + o_beta[q];
+    }
+    c->b = (double*)(w + o_b);
+    c->e32 = mixed ? (float*)(w + o_e) : nullptr;
+    c->r32 = mixed ? (float*)(w + o_r) : nullptr;
+    c->nlev = nl;
+    for (int l = 0; l < nl; ++l) c->shp[l] = lv[l];
+    for (int l = 1; l < nl; ++l) {
+      c->lx[l] = w + o_lx[l];
+      c->lb[l] = w + o_lb[l];
+      for (int q = 0; q < 3; ++q) c->lbeta[l][q] = w + o_lbeta[l][q];
+    }
+    for (int q = 0; q < 3; ++q) c->cg[q] = w + o_cg[q];
+    c->partial = (double*)(w + o_part);
+    c->scal = (double*)(w + o_scal);
+    c->maxbits = (unsigned long long*)(w + o_max);
+    c->flags = (int*)(w + o_flags);
+    c->dt_dev = (double*)(w + o_dt);
+    c->lim_dev = (int*)(w + o_lim);
+  }
+  return pl.off;
+}
+
+fvm_status set_err(fvm_ctx* c, fvm_status s, const char* msg) {
+  if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
+  return s;
+}
+
+fvm_status cuda_check(fvm_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+    return FVM_ECUDA;
+  }
+  return FVM_OK;
+}
+
+fvm_status read_scalar(fvm_ctx* c, const double* dsrc, double* host) {
+  cudaError_t e = cudaMemcpyAsync(host, dsrc, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "device read: %s", cudaGetErrorString(e));
+    return FVM_ECUDA;
+  }
+  return FVM_OK;
+}
+
+template <typename T>
+MGLevel<T> mg_level(fvm_ctx* c, int l, T* x, T* b, T* const* beta) {
+  MGLevel<T> L;
+  L.geo = make_geo(c->prm, c->shp[l]);
+  L.x = x;
+  L.b = b;
+  for (int q = 0; q < 3; ++q) L.beta[q] = beta[q];
+  for (int d = 0; d < 3; ++d) L.f[d] = c->shp[l].f[d];
+  return L;
+}
+
+// hierarchy in precision T with level 0 given by (x0, b0, beta0)
+template <typename T>
+void hierarchy(fvm_ctx* c, T* x0, T* b0, T* const* beta0, MGLevel<T>* Ls) {
+  Ls[0] = mg_level<T>(c, 0, x0, b0, beta0);
+  for (int l = 1; l < c->nlev; ++l) {
+    T* be[3] = {(T*)c->lbeta[l][0], (T*)c->lbeta[l][1], (T*)c->lbeta[l][2]};
+    Ls[l] = mg_level<T>(c, l, (T*)c->lx[l], (T*)c->lb[l], be);
+  }
+}
+
+template <typename T>
+void coarsen_betas(fvm_ctx* c, MGLevel<T>* Ls) {
+  for (int l = 0; l + 1 < c->nlev; ++l)
+    TIMED(c, FVM_K_BETA, 1, launch_beta_coarsen<T>(Ls[l], Ls[l + 1], c->stream));
+}
+
+template <typename T>
+void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
+  cudaStream_t s = c->stream;
+  if (l == c->nlev - 1) {
+    TIMED(c, FVM_K_COARSE_CG, 1, launch_coarse_cg<T>(Ls[l], (T*)c->cg[0], (T*)c->cg[1], (T*)c->cg[2],
+                                                   coarse_rtol, c->prm.coarse_maxit, s));
+    return;
+  }
+  const int kg = l == 0 ? FVM_K_GS_FINE : FVM_K_GS_COARSE;
+  for (int q = 0; q < c->prm.mg_pre; ++q) {
+    TIMED(c, kg, 1, launch_gs<T>(Ls[l], 0, s));
+    TIMED(c, kg, 1, launch_gs<T>(Ls[l], 1, s));
+  }
+  TIMED(c, l == 0 ? FVM_K_RESTRICT_FINE : FVM_K_RESTRICT_COARSE, 1,
+        launch_residual_restrict<T>(Ls[l], Ls[l + 1], s));
+  vcycle<T>(c, Ls, l + 1, coarse_rtol);
+  TIMED(c, l == 0 ? FVM_K_PROLONG_FINE : FVM_K_PROLONG_COARSE, 1,
+        launch_prolong<T>(Ls[l], Ls[l + 1], s));
+  for (int q = 0; q < c->prm.mg_post; ++q) {
+    TIMED(c, kg, 1, launch_gs<T>(Ls[l], 1, s));
+    TIMED(c, kg, 1, launch_gs<T>(Ls[l], 0, s));
+  }
+}
+
+// F64: L p = b (b mean-free, double), beta0 already computed
+fvm_status solve_f64(fvm_ctx* c, double* p, double* b, int* cycles_out, double* rel_out,
+                     bool want_rel) {
+  cudaStream_t s = c->stream;
+  MGLevel<double> Ls[kMaxLevels];
+  double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};
+  hierarchy<double>(c, p, b, be, Ls);
+  coarsen_betas<double>(c, Ls);
+  const long long N = c->g.N;
+  double bn2;
+  TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(b, N, true, c->partial, c->scal + 0, s));
+  fvm_status st = read_scalar(c, c->scal + 0, &bn2);
+  if (st) return st;
+  if (!isfinite(bn2)) return set_err(c, FVM_EUNSTABLE, "non-finite projection right-hand side");
+  double bn = sqrt(bn2);
+  int cycles = 0;
+  double rel = 0.0;
+  if (bn == 0.0) {
+    TIMED(c, FVM_K_MISC, 1, launch_zero<double>(p, N, s));
+    *cycles_out = 0;
+    *rel_out = 0.0;
+    return cuda_check(c, "poisson zero");
+  }
+  const int fixed = c->prm.mg_fixed_cycles;
+  if (fixed > 0) {
+    for (int q = 0; q < fixed; ++q) vcycle<double>(c, Ls, 0, c->prm.coarse_rtol);
+    cycles = fixed;
+    if (want_rel) {
+      double r2;
+      TIMED(c, FVM_K_RESNORM, 2, launch_residual_norm2<double>(Ls[0], c->partial, c->scal + 1, s));
+      st = read_scalar(c, c->scal + 1, &r2);
+      if (st) return st;
+      rel = sqrt(r2) / bn;
+    }
+  } else {
+    for (;;) {
+      double r2;
+      TIMED(c, FVM_K_RESNORM, 2, launch_residual_norm2<double>(Ls[0], c->partial, c->scal + 1, s));
+      st = read_scalar(c, c->scal + 1, &r2);
+      if (st) return st;
+      rel = sqrt(r2) / bn;
+      if (!isfinite(rel)) return set_err(c, FVM_EUNSTABLE, "non-finite pressure residual");
+      if (rel <= c->prm.mg_rtol || cycles >= c->prm.mg_max_cycles) break;
+      vcycle<double>(c, Ls, 0, c->prm.coarse_rtol);
+      ++cycles;
+    }
+  }
+  TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(p, N, false, c->partial, c->scal + 2, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sub_mean(p, N, c->scal + 2, s));
+  *cycles_out = cycles;
+  *rel_out = rel;
+  st = cuda_check(c, "f64 pressure solve");
+  if (st) return st;
+  if (fixed == 0 && rel > c->prm.mg_rtol)
+    return set_err(c, FVM_ENOCONV, "pressure solve reached mg_max_cycles above mg_rtol");
+  return FVM_OK;
+}
+
+// MIXED: double defect correction around float V-cycles
+fvm_status solve_mixed(fvm_ctx* c, double* p, double* b, int* cycles_out, double* rel_out,
+                       bool want_rel) {
+  (void)want_rel;
+  cudaStream_t s = c->stream;
+  MGLevel<float> Ls[kMaxLevels];
+  float* be[3] = {(float*)c->beta0[0], (float*)c->beta0[1], (float*)c->beta0[2]};
+  hierarchy<float>(c, c->e32, c->r32, be, Ls);
+  coarsen_betas<float>(c, Ls);
+  const long long N = c->g.N;
+  double bn2;
+  TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(b, N, true, c->partial, c->scal + 0, s));
+  fvm_status st = read_scalar(c, c->scal + 0, &bn2);
+  if (st) return st;
+  if (!isfinite(bn2)) return set_err(c, FVM_EUNSTABLE, "non-finite projection right-hand side");
+  double bn = sqrt(bn2);
+  if (bn == 0.0) {
+    TIMED(c, FVM_K_MISC, 1, launch_zero<double>(p, N, s));
+    *cycles_out = 0;
+    *rel_out = 0.0;
+    return cuda_check(c, "poisson zero");
+  }
+  const int fixed = c->prm.mg_fixed_cycles;
+  const double crtol = c->prm.coarse_rtol > 1e-6 ? c->prm.coarse_rtol : 1e-6;
+  int outer = 0;
+  double rel = 0.0;
+  for (;;) {
+    TIMED(c, FVM_K_RESIDUAL64, 2, launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, s));
+    if (fixed > 0) {
+      if (outer == fixed) {
+        double r2;
+        st = read_scalar(c, c->scal + 1, &r2);
+        if (st) return st;
+        rel = sqrt(r2) / bn;
+        break;
+      }
+    } else {
+      double r2;
+      st = read_scalar(c, c->scal + 1, &r2);
+      if (st) return st;
+      rel = sqrt(r2) / bn;
+      if (!isfinite(rel)) return set_err(c, FVM_EUNSTABLE, "non-finite pressure residual");
+      if (rel <= c->prm.mg_rtol || outer >= c->prm.mg_max_cycles) break;
+    }
+    TIMED(c, FVM_K_MISC, 1, launch_zero<float>(c->e32, N, s));
+    for (int q = 0; q < c->prm.mx_inner_cycles; ++q) vcycle<float>(c, Ls, 0, crtol);
+    TIMED(c, FVM_K_ADD_CORRECTION, 1, launch_add_correction(N, p, c->e32, s));
+    ++outer;
+  }
+  TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(p, N, false, c->partial, c->scal + 2, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sub_mean(p, N, c->scal + 2, s));
+  *cycles_out = outer;
+  *rel_out = rel;
+  st = cuda_check(c, "mixed pressure solve");
+  if (st) return st;
+  if (fixed == 0 && rel > c->prm.mg_rtol)
+    return set_err(c, FVM_ENOCONV, "pressure solve reached mg_max_cycles above mg_rtol");
+  return FVM_OK;
+}
+
+template <typename R>
+Fields<R> fields_of(void* const* a) {
+  Fields<R> f;
+  f.u[0] = (R*)a[0];
+  f.u[1] = (R*)a[1];
+  f.u[2] = (R*)a[2];
+  f.alpha = (R*)a[3];
+  f.T = (R*)a[4];
+  return f;
+}
+
+// one forward-Euler stage E(X) and Y = a Sn + b E(X)
+template <typename R>
+fvm_status stage(fvm_ctx* c, Fields<R> X, Fields<R> Sn, Fields<R> Y, double* p, double ca,
+                 double cb, double xc, int* cyc, double* rel, bool want_rel) {
+  cudaStream_t s = c->stream;
+  const Geo& g = c->g;
+  // smoothed phase fraction
+  const R* src = X.alpha;
+  int passes = c->prm.smooth_passes;
+  for (int q = 0; q < passes; ++q) {
+    R* dst = ((passes - q) % 2 == 1) ? (R*)c->as : (R*)c->tmp;
+    TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<R>(g, src, dst, s));
+    src = dst;
+  }
+  const R* as = passes > 0 ? (const R*)c->as : X.alpha;
+  R* M[3] = {(R*)c->M[0], (R*)c->M[1], (R*)c->M[2]};
+  R* us[3] = {(R*)c->us[0], (R*)c->us[1], (R*)c->us[2]};
+  TIMED(c, FVM_K_INTERFACE, 1, launch_interface<R>(g, c->ph, c->tb, X.alpha, as, X.T, (R*)c->kappa,
+                                                M[0], M[1], M[2], s));
+  TIMED(c, FVM_K_SCALARS, 1, launch_scalars<R>(g, c->ph, c->tb, X, Sn, Y, c->dt_dev, ca, cb, xc, s));
+  TIMED(c, FVM_K_MOMENTUM, 1, launch_momentum<R>(g, c->ph, c->tb, X, (R*)c->kappa, M[0], M[1], M[2],
+                                              us[0], us[1], us[2], c->dt_dev, s));
+  TIMED(c, FVM_K_DIV_RHS, 1, launch_div_rhs<R>(g, us, c->dt_dev, c->b, c->partial, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sum_partials(c->partial, kRedBlocks, c->scal + 3, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sub_mean(c->b, g.N, c->scal + 3, s));
+  fvm_status st;
+  if (c->mixed) {
+    float* be[3] = {(float*)c->beta0[0], (float*)c->beta0[1], (float*)c->beta0[2]};
+    TIMED(c, FVM_K_BETA, 1, launch_beta<R, float>(g, c->ph, (const R*)X.alpha, be[0], be[1], be[2], s));
+    st = solve_mixed(c, p, c->b, cyc, rel, want_rel);
+    if (st && st != FVM_ENOCONV) return st;
+    TIMED(c, FVM_K_CORRECT, 1, launch_correct<R, float>(g, Sn, Y, us, p, be, c->dt_dev, ca, cb, s));
+  } else {
+    double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};
+    TIMED(c, FVM_K_BETA, 1, launch_beta<R, double>(g, c->ph, (const R*)X.alpha, be[0], be[1], be[2], s));
+    st = solve_f64(c, p, c->b, cyc, rel, want_rel);
+    if (st && st != FVM_ENOCONV) return st;
+    TIMED(c, FVM_K_CORRECT, 1, launch_correct<R, double>(g, Sn, Y, us, p, be, c->dt_dev, ca, cb, s));
+  }
+  fvm_status st2 = cuda_check(c, "stage");
+  return st2 ? st2 : st;
+}
+
+template <typename R>
+fvm_status step_impl(fvm_ctx* c, fvm_state* st, long step_index, double dt_in,
+                     fvm_step_info* info) {
+  cudaStream_t s = c->stream;
+  void* sp[5] = {st->u, st->v, st->w, st->alpha, st->T};
+  Fields<R> Sn = fields_of<R>(sp);
+  Fields<R> A = fields_of<R>(c->A);
+  Fields<R> B = fields_of<R>(c->B);
+  int limiter = -1;
+  if (dt_in > 0.0) {
+    TIMED(c, FVM_K_DT, 1, launch_set_scalar(c->dt_dev, dt_in, s));
+  } else {
+    TIMED(c, FVM_K_DT, 1, launch_dt_reduce<R>(c->g, c->ph, Sn, c->maxbits, c->flags, s));
+    TIMED(c, FVM_K_DT, 1,
+          launch_dt_final(c->g, c->ph, c->prm.cfl, c->prm.c_cap, c->prm.c_visc, c->prm.c_therm,
+                          c->prm.dt_max, c->maxbits, c->dt_dev, c->lim_dev, s));
+  }
+  static const double RK[3][3] = {{0.0, 1.0, 0.0}, {0.75, 0.25, 1.0}, {1.0 / 3.0, 2.0 / 3.0, 0.5}};
+  Fields<R> Xs[3] = {Sn, A, B};
+  Fields<R> Ys[3] = {A, B, Sn};
+  int cyc[3] = {0, 0, 0};
+  double rel[3] = {0, 0, 0};
+  fvm_status worst = FVM_OK;
+  const bool want_rel = info != nullptr;
+  for (int q = 0; q < 3; ++q) {
+    double xc = c->prm.q_x0 + c->prm.q_speed * c->prm.h * ((double)step_index + RK[q][2]);
+    fvm_status r = stage<R>(c, Xs[q], Sn, Ys[q], st->p, RK[q][0], RK[q][1], xc, &cyc[q],
+                            &rel[q], want_rel);
+    if (r == FVM_ENOCONV) worst = r;
+    else if (r) return r;
+  }
+  if (info) {
+    TIMED(c, FVM_K_DIAGNOSTICS, 1,
+          launch_diagnostics<R>(c->g, c->ph, Sn, st->p, c->dt_dev, c->partial, c->maxbits, c->flags, s));
+    TIMED(c, FVM_K_DIAGNOSTICS, 1, launch_sum_partials(c->partial, kRedBlocks, c->scal + 4, s));
+    TIMED(c, FVM_K_DIAGNOSTICS, 1,
+          launch_sum_partials(c->partial + kRedBlocks, kRedBlocks, c->scal + 5, s));
+    double hs[2], dt;
+    unsigned long long mb;
+    int flag, lim;
+    cudaError_t e = cudaMemcpyAsync(hs, c->scal + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&mb, c->maxbits, sizeof(mb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&dt, c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&lim, c->lim_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_err(c, FVM_ECUDA, cudaGetErrorString(e));
+    double mdiv;
+    memcpy(&mdiv, &mb, sizeof(double));
+    double h3 = c->prm.h * c->prm.h * c->prm.h;
+    info->dt = dt;
+    info->dt_limiter = dt_in > 0.0 ? -1 : lim;
+    for (int q = 0; q < 3; ++q) {
+      info->vcycles[q] = cyc[q];
+      info->rel_residual[q] = rel[q];
+    }
+    info->max_div_dt = mdiv * dt;
+    info->vol_sum = hs[0] * h3;
+    info->mass_sum = hs[1] * h3;
+    info->nan_flag = flag;
+    if (flag) return set_err(c, FVM_EUNSTABLE, "NaN or Inf in the new state");
+  }
+  (void)limiter;
+  fvm_status e2 = cuda_check(c, "step");
+  return e2 ? e2 : worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+fvm_status fvm_workspace_size(const fvm_params* prm, size_t* bytes) {
+  if (!bytes) return FVM_EINVAL;
+  if (check_params(prm)) return FVM_EINVAL;
+  *bytes = plan_workspace(*prm, nullptr);
+  return FVM_OK;
+}
+
+fvm_status fvm_create(const fvm_params* prm, void* workspace, size_t bytes, void* cuda_stream,
+                      fvm_ctx** out) {
+  if (!out) return FVM_EINVAL;
+  *out = nullptr;
+  if (check_params(prm)) return FVM_EINVAL;
+  size_t need = plan_workspace(*prm, nullptr);
+  if (!workspace) return FVM_EINVAL;
+  if (((uintptr_t)workspace) % kAlign) return FVM_EINVAL;
+  if (bytes < need) return FVM_ENOMEM;
+  fvm_ctx* c = new (std::nothrow) fvm_ctx;
+  if (!c) return FVM_ENOMEM;
+  memset(c, 0, sizeof(*c));
+  c->prm = *prm;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->mixed = prm->precision == FVM_MIXED;
+  c->rsz = c->mixed ? sizeof(float) : sizeof(double);
+  c->ws = (char*)workspace;
+  c->ws_bytes = bytes;
+  plan_workspace(*prm, c);
+  c->g = make_geo(*prm, c->shp[0]);
+  Phys& ph = c->ph;
+  for (int q = 0; q < 2; ++q) {
+    ph.rho[q] = prm->rho[q];
+    ph.mu[q] = prm->mu[q];
+    ph.lam[q] = prm->lambda[q];
+    ph.rcp[q] = prm->rho[q] * prm->cp[q];
+  }
+  ph.sigma0 = prm->sigma0;
+  ph.dsdT = prm->dsigma_dT;
+  ph.T0 = prm->T0;
+  for (int d = 0; d < 3; ++d) ph.g[d] = prm->g[d];
+  ph.q_power = prm->q_power;
+  ph.q_radius = prm->q_radius;
+  ph.q_x0 = prm->q_x0;
+  ph.q_y0 = prm->q_y0;
+  ph.q_speed = prm->q_speed;
+  ph.eps_a = prm->weno_eps * prm->weno_scale[0] * prm->weno_scale[0];
+  ph.eps_T = prm->weno_eps * prm->weno_scale[1] * prm->weno_scale[1];
+  ph.eps_u = prm->weno_eps * prm->weno_scale[2] * prm->weno_scale[2];
+  ph.eps_n = 1e-8 / prm->h;
+  ph.L[0] = prm->nx * prm->h;
+  ph.L[1] = prm->ny * prm->h;
+  ph.L[2] = prm->nz * prm->h;
+  TBC& tb = c->tb;
+  tb.axis = -1;
+  for (int d = 0; d < 3; ++d) {
+    bool dl = prm->tbc[2 * d] == FVM_TBC_DIRICHLET, dh = prm->tbc[2 * d + 1] == FVM_TBC_DIRICHLET;
+    if (dl || dh) {
+      tb.axis = d;
+      tb.dir[0] = dl;
+      tb.dir[1] = dh;
+      tb.T0[0] = prm->tbc_T0[2 * d];
+      tb.T0[1] = prm->tbc_T0[2 * d + 1];
+      tb.amp[0] = prm->tbc_dTamp[2 * d];
+      tb.amp[1] = prm->tbc_dTamp[2 * d + 1];
+      tb.s_axis = d == 0 ? 1 : 0;
+      tb.Ls = ph.L[tb.s_axis];
+    }
+  }
+  snprintf(c->err, sizeof(c->err), "ok");
+  *out = c;
+  return FVM_OK;
+}
+
+fvm_status fvm_destroy(fvm_ctx* ctx) {
+  if (!ctx) return FVM_EINVAL;
+  if (ctx->prof_ev) {
+    for (int q = 0; q < 2 * kProfSlots; ++q) cudaEventDestroy(ctx->prof_ev[q]);
+    free(ctx->prof_ev);
+    free(ctx->prof_cls);
+  }
+  delete ctx;
+  return FVM_OK;
+}
+
+fvm_status fvm_profile(fvm_ctx* ctx, int on) {
+  if (!ctx) return FVM_EINVAL;
+  if (on && !ctx->prof_ev) {
+    ctx->prof_ev = (cudaEvent_t*)calloc(2 * kProfSlots, sizeof(cudaEvent_t));
+    ctx->prof_cls = (int*)calloc(kProfSlots, sizeof(int));
+    if (!ctx->prof_ev || !ctx->prof_cls) return set_err(ctx, FVM_ENOMEM, "host allocation failed");
+    for (int q = 0; q < 2 * kProfSlots; ++q)
+      if (cudaEventCreate(&ctx->prof_ev[q]) != cudaSuccess)
+        return set_err(ctx, FVM_ECUDA, "cudaEventCreate failed");
+  }
+  if (!on) prof_fold(ctx);
+  if (on) {
+    prof_fold(ctx);
+    for (int q = 0; q < FVM_KCLASS_COUNT; ++q) {
+      ctx->prof_launches[q] = 0;
+      ctx->prof_ms[q] = 0.0;
+    }
+  }
+  ctx->prof = on ? 1 : 0;
+  return FVM_OK;
+}
+
+fvm_status fvm_launch_count(fvm_ctx* ctx, int reset, long* count) {
+  if (!ctx || !count) return FVM_EINVAL;
+  *count = ctx->nlaunch;
+  if (reset) ctx->nlaunch = 0;
+  return FVM_OK;
+}
+
+fvm_status fvm_profile_read(fvm_ctx* ctx, int kernel_class, long* launches, double* total_ms) {
+  if (!ctx || kernel_class < 0 || kernel_class >= FVM_KCLASS_COUNT || !launches || !total_ms)
+    return FVM_EINVAL;
+  prof_fold(ctx);
+  *launches = ctx->prof_launches[kernel_class];
+  *total_ms = ctx->prof_ms[kernel_class];
+  return FVM_OK;
+}
+
+fvm_status fvm_step(fvm_ctx* ctx, fvm_state* st, long step_index, double dt, fvm_step_info* info) {
+  if (!ctx) return FVM_EINVAL;
+  if (!st || !st->u || !st->v || !st->w || !st->alpha || !st->T || !st->p)
+    return set_err(ctx, FVM_EINVAL, "null state pointer");
+  if (!(dt == dt)) return set_err(ctx, FVM_EINVAL, "dt is NaN");
+  cudaGetLastError();
+  if (ctx->mixed) return step_impl<float>(ctx, st, step_index, dt, info);
+  return step_impl<double>(ctx, st, step_index, dt, info);
+}
+
+fvm_status fvm_poisson_solve(fvm_ctx* ctx, const void* alpha, const double* rhs, double* p,
+                             fvm_step_info* info) {
+  if (!ctx) return FVM_EINVAL;
+  if (!alpha || !rhs || !p) return set_err(ctx, FVM_EINVAL, "null pointer");
+  cudaGetLastError();
+  cudaStream_t s = ctx->stream;
+  const Geo& g = ctx->g;
+  cudaError_t e = cudaMemcpyAsync(ctx->b, rhs, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return set_err(ctx, FVM_ECUDA, cudaGetErrorString(e));
+  TIMED(ctx, FVM_K_MISC, 2, launch_sum_field<double>(ctx->b, g.N, false, ctx->partial, ctx->scal + 3, s));
+  TIMED(ctx, FVM_K_MISC, 1, launch_sub_mean(ctx->b, g.N, ctx->scal + 3, s));
+  int cyc = 0;
+  double rel = 0.0;
+  fvm_status st;
+  if (ctx->mixed) {
+    float* be[3] = {(float*)ctx->beta0[0], (float*)ctx->beta0[1], (float*)ctx->beta0[2]};
+    TIMED(ctx, FVM_K_BETA, 1, launch_beta<float, float>(g, ctx->ph, (const float*)alpha, be[0], be[1], be[2], s));
+    st = solve_mixed(ctx, p, ctx->b, &cyc, &rel, info != nullptr);
+  } else {
+    double* be[3] = {(double*)ctx->beta0[0], (double*)ctx->beta0[1], (double*)ctx->beta0[2]};
+    TIMED(ctx, FVM_K_BETA, 1, launch_beta<double, double>(g, ctx->ph, (const double*)alpha, be[0], be[1], be[2], s));
+    st = solve_f64(ctx, p, ctx->b, &cyc, &rel, info != nullptr);
+  }
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->vcycles[0] = cyc;
+    info->rel_residual[0] = rel;
+    info->dt_limiter = -1;
+  }
+  if (st) return st;
+  return cuda_check(ctx, "poisson");
+}
+
+fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index, double dt,
+                            const fvm_state* lam_np1, fvm_state* lam_n, double dtheta[2]) {
+  (void)st_n; (void)step_index; (void)dt; (void)lam_np1; (void)lam_n; (void)dtheta;
+  if (!ctx) return FVM_EINVAL;
+  return set_err(ctx, FVM_EUNSUPPORTED, "the adjoint step is not implemented");
+}
+
+const char* fvm_status_string(fvm_status s) {
+  switch (s) {
+    case FVM_OK: return "ok";
+    case FVM_EINVAL: return "invalid argument";
+    case FVM_ENOMEM: return "workspace too small";
+    case FVM_ECUDA: return "CUDA error";
+    case FVM_ENOCONV: return "pressure solve did not converge";
+    case FVM_EUNSTABLE: return "non-finite values";
+    case FVM_ETIMEOUT: return "device wait timed out";
+    case FVM_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* fvm_last_error(const fvm_ctx* ctx) { return ctx ? ctx->err : "no context"; }
+
+const char* fvm_version(void) { return "fvm-gb300 0.1"; }
+
+}  // extern "C"

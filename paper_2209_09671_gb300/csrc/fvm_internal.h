@@ -1,0 +1,135 @@
+// Internal declarations shared by the translation units of libfvm.
+// Host-side launchers are declared here; kernels live in fvm_stage.cu
+// (one forward-Euler stage: smoothing, interface geometry, scalar transport,
+// momentum predictor, projection right-hand side, correction) and fvm_mg.cu
+// (geometric multigrid, reductions).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/fvm.h"
+
+namespace fvm {
+
+enum { PER = 0, WALL = 1 };
+
+// Geometry of one grid level.
+struct Geo {
+  int n[3];          // cells per axis x, y, z
+  int bc[3];         // PER or WALL per axis
+  double h;          // cell edge of the finest level (fine kernels)
+  double hd[3];      // cell edge per axis on this level (multigrid)
+  long long sy, sz;  // strides of y and z
+  long long N;       // cell count
+};
+
+// Dirichlet temperature walls (at most one axis carries them).
+struct TBC {
+  int axis;           // -1: no Dirichlet side
+  int dir[2];         // 1 if the low / high side of `axis` is Dirichlet
+  double T0[2], amp[2];
+  int s_axis;         // tangential coordinate of the cosine
+  double Ls;          // domain length along s_axis
+};
+
+// Material and source parameters (in the form the kernels use).
+struct Phys {
+  double rho[2], mu[2], lam[2], rcp[2];   // rcp = rho * cp per phase
+  double sigma0, dsdT, T0;
+  double g[3];
+  double q_power, q_radius, q_x0, q_y0, q_speed;
+  double eps_a, eps_T, eps_u;             // WENO eps per field
+  double eps_n;                           // normal regulariser 1e-8 / h
+  double L[3];                            // domain lengths
+};
+
+// Pointers of one state (u, v, w, alpha, T) in the working precision R.
+template <typename R>
+struct Fields {
+  R* u[3];
+  R* alpha;
+  R* T;
+};
+
+// One multigrid level in precision T.
+template <typename T>
+struct MGLevel {
+  Geo geo;
+  T* x;
+  T* b;
+  T* beta[3];
+  int f[3];          // coarsening factor to the next level
+};
+
+constexpr int kMaxLevels = 24;
+constexpr int kRedBlocks = 1024;   // partial-sum slots of the two-pass reductions
+
+// ----- stage launchers (fvm_stage.cu) --------------------------------------
+template <typename R>
+void launch_smooth(const Geo& g, const R* in, R* out, cudaStream_t s);
+template <typename R>
+void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, const R* alpha,
+                      const R* alpha_s, const R* T, R* kappa, R* M0, R* M1, R* M2,
+                      cudaStream_t s);
+template <typename R>
+void launch_scalars(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, Fields<R> Sn,
+                    Fields<R> Y, const double* dt, double a, double b, double xc_shift,
+                    cudaStream_t s);
+template <typename R>
+void launch_momentum(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, const R* kappa,
+                     const R* M0, const R* M1, const R* M2, R* us0, R* us1, R* us2,
+                     const double* dt, cudaStream_t s);
+template <typename R>
+void launch_div_rhs(const Geo& g, R* const* us, const double* dt, double* b, double* partial,
+                    cudaStream_t s);
+template <typename R, typename B>
+void launch_beta(const Geo& g, const Phys& ph, const R* alpha, B* b0, B* b1, B* b2,
+                 cudaStream_t s);
+template <typename R, typename B>
+void launch_correct(const Geo& g, Fields<R> Sn, Fields<R> Y, R* const* us, const double* p,
+                    B* const* beta, const double* dt, double a, double b, cudaStream_t s);
+template <typename R>
+void launch_dt_reduce(const Geo& g, const Phys& ph, Fields<R> X, unsigned long long* maxbits,
+                      int* nanflag, cudaStream_t s);
+void launch_dt_final(const Geo& g, const Phys& ph, double cfl, double c_cap, double c_visc,
+                     double c_therm, double dt_max, const unsigned long long* maxbits,
+                     double* dt, int* limiter, cudaStream_t s);
+void launch_set_scalar(double* dst, double v, cudaStream_t s);
+template <typename R>
+void launch_diagnostics(const Geo& g, const Phys& ph, Fields<R> X, const double* p,
+                        const double* dt, double* partial, unsigned long long* maxbits,
+                        int* nanflag, cudaStream_t s);
+
+// ----- reductions and multigrid (fvm_mg.cu) ----------------------------------
+// Deterministic two-pass sums: per-block partial sums in `partial`, then one
+// block adds them in a fixed order into *out.
+void launch_sum_partials(const double* partial, int nparts, double* out, cudaStream_t s);
+template <typename T>
+void launch_sum_field(const T* a, long long n, bool squares, double* partial, double* out,
+                      cudaStream_t s);
+void launch_sub_mean(double* a, long long n, const double* sum, cudaStream_t s);
+template <typename T>
+void launch_zero(T* a, long long n, cudaStream_t s);
+
+template <typename T>
+void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s);
+template <typename T>
+void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
+template <typename T>
+void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
+template <typename T>
+void launch_beta_coarsen(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
+template <typename T>
+void launch_coarse_cg(const MGLevel<T>& L, T* r, T* d, T* Ad, double rtol, int maxit,
+                      cudaStream_t s);
+// ||b - L x||^2 into *out (double), x, b, beta in precision T
+template <typename T>
+void launch_residual_norm2(const MGLevel<T>& L, double* partial, double* out, cudaStream_t s);
+// Mixed form: r = b - L p in double with float beta; writes r32 and ||r||^2
+void launch_residual64(const Geo& g, const double* p, const double* b, float* const* beta,
+                       float* r32, double* partial, double* out, cudaStream_t s);
+void launch_add_correction(long long n, double* p, const float* e, cudaStream_t s);
+
+}  // namespace fvm

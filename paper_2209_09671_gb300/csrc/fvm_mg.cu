@@ -1,0 +1,411 @@
+// Geometric multigrid for the density-weighted pressure operator
+//   (L x)_c = sum_faces beta_f (x_c - x_nb) / h_d^2
+// and the deterministic reductions the solver and the step use.
+//   k_gs                red-black Gauss-Seidel sweep of one colour (i+j+k mod 2)
+//   k_residual_restrict residual on the fine level, mean over the children
+//   k_prolong           piecewise-constant prolongation, added to the fine level
+//   k_beta_coarsen      coarse face beta = mean of the fine faces it covers
+//   k_coarse_cg         conjugate gradients on the coarsest level, one CTA
+//   k_residual_norm2    ||b - L x||^2 partial sums
+//   k_residual64        mixed form: r = b - L p in double, stored as float
+// The paper names no linear solver; this is the reading used throughout the
+// library: V(pre, post) cycles, red first before and black first after the
+// coarse correction so that the cycle is a symmetric operator.
+#include "fvm_device.cuh"
+
+namespace fvm {
+
+static inline unsigned grid1d(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block sum, result broadcast to every thread
+__device__ double block_sum_all(double v, double* sh) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    double t = (lane < nw) ? sh[lane] : 0.0;
+    t = warp_sum_d(t);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_sum_field(const T* __restrict__ a, long long n, int squares,
+                            double* __restrict__ partial) {
+  __shared__ double sh[33];
+  double acc = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    double v = (double)a[c];
+    acc += squares ? v * v : v;
+  }
+  double s = block_sum_all(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int nparts,
+                               double* __restrict__ out) {
+  __shared__ double sh[33];
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) acc += partial[q];
+  double s = block_sum_all(acc, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+void launch_sum_partials(const double* partial, int nparts, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, 1024, 0, s>>>(partial, nparts, out);
+}
+
+template <typename T>
+void launch_sum_field(const T* a, long long n, bool squares, double* partial, double* out,
+                      cudaStream_t s) {
+  k_sum_field<T><<<kRedBlocks, 256, 0, s>>>(a, n, squares ? 1 : 0, partial);
+  launch_sum_partials(partial, kRedBlocks, out, s);
+}
+
+__global__ void k_sub_mean(double* __restrict__ a, long long n, const double* __restrict__ sum) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  a[c] = a[c] - (*sum) / (double)n;
+}
+
+void launch_sub_mean(double* a, long long n, const double* sum, cudaStream_t s) {
+  k_sub_mean<<<grid1d(n, 256), 256, 0, s>>>(a, n, sum);
+}
+
+template <typename T>
+__global__ void k_zero(T* __restrict__ a, long long n) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < n) a[c] = T(0);
+}
+
+template <typename T>
+void launch_zero(T* a, long long n, cudaStream_t s) {
+  k_zero<T><<<grid1d(n, 256), 256, 0, s>>>(a, n);
+}
+
+// ---------------------------------------------------------------------------
+// operator pieces on a level
+template <typename T>
+struct OpNb {
+  long long lo[3], hi[3];
+  T blo[3], bhi[3];
+};
+
+template <typename T>
+__device__ __forceinline__ void neighbours(const MGLevel<T>& L, int i, int j, int k, long long c,
+                                           OpNb<T>& nb) {
+  const Geo& g = L.geo;
+  int idx[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int n = g.n[d];
+    int lo = idx[d] - 1 < 0 ? idx[d] - 1 + n : idx[d] - 1;
+    int hi = idx[d] + 1 >= n ? idx[d] + 1 - n : idx[d] + 1;
+    int m[3] = {i, j, k};
+    m[d] = lo;
+    nb.lo[d] = lin(g, m[0], m[1], m[2]);
+    m[d] = hi;
+    nb.hi[d] = lin(g, m[0], m[1], m[2]);
+    nb.blo[d] = L.beta[d][c];
+    nb.bhi[d] = (g.bc[d] == WALL && idx[d] == n - 1) ? T(0) : L.beta[d][nb.hi[d]];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T apply_L_at(const MGLevel<T>& L, const T* __restrict__ x, long long c,
+                                        const OpNb<T>& nb) {
+  const Geo& g = L.geo;
+  T xc = x[c];
+  T out = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (g.n[d] == 1) continue;
+    T w = (T)(1.0 / (g.hd[d] * g.hd[d]));
+    out += (nb.blo[d] * (xc - x[nb.lo[d]]) + nb.bhi[d] * (xc - x[nb.hi[d]])) * w;
+  }
+  return out;
+}
+
+__device__ __forceinline__ void decode_lv(const Geo& g, long long c, int& i, int& j, int& k) {
+  long long q = c / g.n[0];
+  i = (int)(c - q * g.n[0]);
+  k = (int)(q / g.n[1]);
+  j = (int)(q - (long long)k * g.n[1]);
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_gs(MGLevel<T> L, int colour) {
+  const Geo& g = L.geo;
+  int hx = (g.n[0] + 1) >> 1;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long rows = (long long)g.n[1] * g.n[2];
+  if (t >= rows * hx) return;
+  long long row = t / hx;
+  int i2 = (int)(t - row * hx);
+  int k = (int)(row / g.n[1]);
+  int j = (int)(row - (long long)k * g.n[1]);
+  int i = 2 * i2 + ((colour + j + k) & 1);
+  if (i >= g.n[0]) return;
+  long long c = lin(g, i, j, k);
+  OpNb<T> nb;
+  neighbours(L, i, j, k, c, nb);
+  T num = L.b[c];
+  T den = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (g.n[d] == 1) continue;
+    T w = (T)(1.0 / (g.hd[d] * g.hd[d]));
+    num += (nb.blo[d] * L.x[nb.lo[d]] + nb.bhi[d] * L.x[nb.hi[d]]) * w;
+    den += (nb.blo[d] + nb.bhi[d]) * w;
+  }
+  L.x[c] = num / den;
+}
+
+template <typename T>
+void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s) {
+  long long n = (long long)((L.geo.n[0] + 1) / 2) * L.geo.n[1] * L.geo.n[2];
+  k_gs<T><<<grid1d(n, 256), 256, 0, s>>>(L, colour);
+}
+
+// coarse b = mean over children of (b - L x) on the fine level; coarse x = 0
+template <typename T>
+__global__ void k_residual_restrict(MGLevel<T> F, MGLevel<T> C) {
+  long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (cc >= C.geo.N) return;
+  int I, J, K;
+  decode_lv(C.geo, cc, I, J, K);
+  T acc = T(0);
+  int cnt = 0;
+  for (int dz = 0; dz < F.f[2]; ++dz)
+    for (int dy = 0; dy < F.f[1]; ++dy)
+      for (int dx = 0; dx < F.f[0]; ++dx) {
+        int i = I * F.f[0] + dx, j = J * F.f[1] + dy, k = K * F.f[2] + dz;
+        long long c = lin(F.geo, i, j, k);
+        OpNb<T> nb;
+        neighbours(F, i, j, k, c, nb);
+        acc += F.b[c] - apply_L_at(F, F.x, c, nb);
+        ++cnt;
+      }
+  C.b[cc] = acc / (T)cnt;
+  C.x[cc] = T(0);
+}
+
+template <typename T>
+void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s) {
+  k_residual_restrict<T><<<grid1d(C.geo.N, 128), 128, 0, s>>>(F, C);
+}
+
+template <typename T>
+__global__ void k_prolong(MGLevel<T> F, MGLevel<T> C) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.geo.N) return;
+  int i, j, k;
+  decode_lv(F.geo, c, i, j, k);
+  long long p = lin(C.geo, i / F.f[0], j / F.f[1], k / F.f[2]);
+  F.x[c] = F.x[c] + C.x[p];
+}
+
+template <typename T>
+void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s) {
+  k_prolong<T><<<grid1d(F.geo.N, 256), 256, 0, s>>>(F, C);
+}
+
+template <typename T>
+__global__ void k_beta_coarsen(MGLevel<T> F, MGLevel<T> C) {
+  long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (cc >= C.geo.N) return;
+  int I, J, K;
+  decode_lv(C.geo, cc, I, J, K);
+  int base[3] = {I * F.f[0], J * F.f[1], K * F.f[2]};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int cnt[3] = {F.f[0], F.f[1], F.f[2]};
+    cnt[d] = 1;
+    T acc = T(0);
+    for (int dz = 0; dz < cnt[2]; ++dz)
+      for (int dy = 0; dy < cnt[1]; ++dy)
+        for (int dx = 0; dx < cnt[0]; ++dx)
+          acc += F.beta[d][lin(F.geo, base[0] + dx, base[1] + dy, base[2] + dz)];
+    C.beta[d][cc] = acc / (T)(cnt[0] * cnt[1] * cnt[2]);
+  }
+}
+
+template <typename T>
+void launch_beta_coarsen(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s) {
+  k_beta_coarsen<T><<<grid1d(C.geo.N, 128), 128, 0, s>>>(F, C);
+}
+
+// ---------------------------------------------------------------------------
+// conjugate gradients on the coarsest level in one CTA: mean-free rhs,
+// x0 = 0, stop at ||r|| <= rtol ||b||, mean-free result
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, T* __restrict__ r,
+                                                    T* __restrict__ dd, T* __restrict__ Ad,
+                                                    double rtol, int maxit) {
+  __shared__ double sh[33];
+  const Geo& g = L.geo;
+  const long long N = g.N;
+  double acc = 0.0;
+  for (long long c = threadIdx.x; c < N; c += blockDim.x) acc += (double)L.b[c];
+  double mean = block_sum_all(acc, sh) / (double)N;
+  acc = 0.0;
+  for (long long c = threadIdx.x; c < N; c += blockDim.x) {
+    T v = (T)((double)L.b[c] - mean);
+    r[c] = v;
+    dd[c] = v;
+    L.x[c] = T(0);
+    acc += (double)v * (double)v;
+  }
+  double rr = block_sum_all(acc, sh);
+  double bn = sqrt(rr);
+  if (bn == 0.0) return;
+  for (int it = 0; it < maxit; ++it) {
+    if (sqrt(rr) <= rtol * bn) break;
+    __syncthreads();
+    acc = 0.0;
+    for (long long c = threadIdx.x; c < N; c += blockDim.x) {
+      int i, j, k;
+      decode_lv(g, c, i, j, k);
+      OpNb<T> nb;
+      neighbours(L, i, j, k, c, nb);
+      T a = apply_L_at(L, dd, c, nb);
+      Ad[c] = a;
+      acc += (double)dd[c] * (double)a;
+    }
+    double pAp = block_sum_all(acc, sh);
+    if (!(pAp > 0.0)) break;   // breakdown (exhausted search direction or rounding)
+    double a = rr / pAp;
+    acc = 0.0;
+    for (long long c = threadIdx.x; c < N; c += blockDim.x) {
+      L.x[c] = (T)((double)L.x[c] + a * (double)dd[c]);
+      T rv = (T)((double)r[c] - a * (double)Ad[c]);
+      r[c] = rv;
+      acc += (double)rv * (double)rv;
+    }
+    double rr_new = block_sum_all(acc, sh);
+    double beta = rr_new / rr;
+    for (long long c = threadIdx.x; c < N; c += blockDim.x)
+      dd[c] = (T)((double)r[c] + beta * (double)dd[c]);
+    rr = rr_new;
+  }
+  __syncthreads();
+  acc = 0.0;
+  for (long long c = threadIdx.x; c < N; c += blockDim.x) acc += (double)L.x[c];
+  double xm = block_sum_all(acc, sh) / (double)N;
+  for (long long c = threadIdx.x; c < N; c += blockDim.x) L.x[c] = (T)((double)L.x[c] - xm);
+}
+
+template <typename T>
+void launch_coarse_cg(const MGLevel<T>& L, T* r, T* d, T* Ad, double rtol, int maxit,
+                      cudaStream_t s) {
+  k_coarse_cg<T><<<1, 1024, 0, s>>>(L, r, d, Ad, rtol, maxit);
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_residual_norm2(MGLevel<T> L, double* __restrict__ partial) {
+  __shared__ double sh[33];
+  double acc = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < L.geo.N;
+       c += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode_lv(L.geo, c, i, j, k);
+    OpNb<T> nb;
+    neighbours(L, i, j, k, c, nb);
+    double r = (double)(L.b[c] - apply_L_at(L, L.x, c, nb));
+    acc += r * r;
+  }
+  double s = block_sum_all(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <typename T>
+void launch_residual_norm2(const MGLevel<T>& L, double* partial, double* out, cudaStream_t s) {
+  k_residual_norm2<T><<<kRedBlocks, 256, 0, s>>>(L, partial);
+  launch_sum_partials(partial, kRedBlocks, out, s);
+}
+
+__global__ void k_residual64(Geo g, const double* __restrict__ p, const double* __restrict__ b,
+                             const float* __restrict__ b0, const float* __restrict__ b1,
+                             const float* __restrict__ b2, float* __restrict__ r32,
+                             double* __restrict__ partial) {
+  __shared__ double sh[33];
+  const float* be[3] = {b0, b1, b2};
+  double acc = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
+       c += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decode_lv(g, c, i, j, k);
+    int idx[3] = {i, j, k};
+    double pc = p[c];
+    double Lp = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int n = g.n[d];
+      if (n == 1) continue;
+      int lo = idx[d] - 1 < 0 ? idx[d] - 1 + n : idx[d] - 1;
+      int hi = idx[d] + 1 >= n ? idx[d] + 1 - n : idx[d] + 1;
+      int m[3] = {i, j, k};
+      m[d] = lo;
+      long long clo = lin(g, m[0], m[1], m[2]);
+      m[d] = hi;
+      long long chi = lin(g, m[0], m[1], m[2]);
+      double blo = (double)be[d][c];
+      double bhi = (g.bc[d] == WALL && idx[d] == n - 1) ? 0.0 : (double)be[d][chi];
+      double w = 1.0 / (g.hd[d] * g.hd[d]);
+      Lp += (blo * (pc - p[clo]) + bhi * (pc - p[chi])) * w;
+    }
+    double r = b[c] - Lp;
+    r32[c] = (float)r;
+    acc += r * r;
+  }
+  double s = block_sum_all(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+void launch_residual64(const Geo& g, const double* p, const double* b, float* const* beta,
+                       float* r32, double* partial, double* out, cudaStream_t s) {
+  k_residual64<<<kRedBlocks, 256, 0, s>>>(g, p, b, beta[0], beta[1], beta[2], r32, partial);
+  launch_sum_partials(partial, kRedBlocks, out, s);
+}
+
+__global__ void k_add_correction(long long n, double* __restrict__ p, const float* __restrict__ e) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < n) p[c] = p[c] + (double)e[c];
+}
+
+void launch_add_correction(long long n, double* p, const float* e, cudaStream_t s) {
+  k_add_correction<<<grid1d(n, 256), 256, 0, s>>>(n, p, e);
+}
+
+#define FVM_MG_INST(T)                                                                       \
+  template void launch_sum_field<T>(const T*, long long, bool, double*, double*,             \
+                                    cudaStream_t);                                           \
+  template void launch_zero<T>(T*, long long, cudaStream_t);                                 \
+  template void launch_gs<T>(const MGLevel<T>&, int, cudaStream_t);                          \
+  template void launch_residual_restrict<T>(const MGLevel<T>&, const MGLevel<T>&,            \
+                                            cudaStream_t);                                   \
+  template void launch_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);       \
+  template void launch_beta_coarsen<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);  \
+  template void launch_coarse_cg<T>(const MGLevel<T>&, T*, T*, T*, double, int,              \
+                                    cudaStream_t);                                           \
+  template void launch_residual_norm2<T>(const MGLevel<T>&, double*, double*, cudaStream_t);
+
+FVM_MG_INST(double)
+FVM_MG_INST(float)
+
+}  // namespace fvm
