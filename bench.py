@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="cells per axis (default 256)")
     ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     return ap.parse_args()
 
 
@@ -283,37 +284,41 @@ def run_ours(args, rank, world, local_rank):
                for k, v in prof.items() if v[0]}
 
     # ---------------- end to end through host buffers -------------------------
-    host = {k: v.to("cpu").pin_memory() for k, v in state.items()}
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = h2d
-    with torch.cuda.stream(stream):
-        for _ in range(2):
-            for k in state:
-                state[k].copy_(host[k], non_blocking=True)
-            solver.fvm_step(state, step_idx, 0.0, info=False)
-            for k in state:
-                host[k].copy_(state[k], non_blocking=True)
-            step_idx += 1
-    stream.synchronize()
-    e2e_steps = max(3, args.steps // 2)
-    barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(e2e_steps):
-            for k in state:
-                state[k].copy_(host[k], non_blocking=True)
-            solver.fvm_step(state, step_idx, 0.0, info=False)
-            for k in state:
-                host[k].copy_(state[k], non_blocking=True)
-            step_idx += 1
-    e1.record(stream)
-    stream.synchronize()
-    barrier()
-    e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3 / e2e_steps)
+    e2e = None
+    if not args.no_e2e:
+        host = {k: v.to("cpu").pin_memory() for k, v in state.items()}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = h2d
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                for k in state:
+                    state[k].copy_(host[k], non_blocking=True)
+                solver.fvm_step(state, step_idx, 0.0, info=False)
+                for k in state:
+                    host[k].copy_(state[k], non_blocking=True)
+                step_idx += 1
+        stream.synchronize()
+        e2e_steps = max(3, args.steps // 2)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(e2e_steps):
+                for k in state:
+                    state[k].copy_(host[k], non_blocking=True)
+                solver.fvm_step(state, step_idx, 0.0, info=False)
+                for k in state:
+                    host[k].copy_(state[k], non_blocking=True)
+                step_idx += 1
+        e1.record(stream)
+        stream.synchronize()
+        barrier()
+        e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3 / e2e_steps)
+        e2e = {"value": world * N / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
     solver.close()
-    del state, host, solver
+    del state, solver
     torch.cuda.empty_cache()
 
     # ---------------- FP64 step (side measurement, same workload) ----------
@@ -357,8 +362,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (state 448 MB)"},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * N / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
         "f64": f64,

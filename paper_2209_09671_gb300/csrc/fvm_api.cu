@@ -69,6 +69,8 @@ Geo make_geo(const fvm_params& p, const LevelShape& s) {
     g.hd[d] = s.hd[d];
   }
   g.h = p.h;
+  g.ih = 1.0 / p.h;
+  for (int d = 0; d < 3; ++d) g.w[d] = g.n[d] > 1 ? 1.0 / (g.hd[d] * g.hd[d]) : 0.0;
   g.sy = g.n[0];
   g.sz = (long long)g.n[0] * g.n[1];
   g.N = g.sz * g.n[2];
@@ -78,6 +80,7 @@ Geo make_geo(const fvm_params& p, const LevelShape& s) {
 const char* check_params(const fvm_params* p) {
   if (!p) return "params is NULL";
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "grid sizes must be >= 1";
+  if ((long long)p->nx * p->ny * p->nz > 2147483647LL) return "more than 2^31-1 cells";
   if (!(p->h > 0.0)) return "h must be > 0";
   int ndir = 0;
   for (int d = 0; d < 3; ++d) {
@@ -100,6 +103,7 @@ const char* check_params(const fvm_params* p) {
     return "multigrid counts out of range";
   if (!(p->mg_rtol > 0.0) || !(p->coarse_rtol > 0.0)) return "tolerances must be > 0";
   if (!(p->weno_eps > 0.0)) return "weno_eps must be > 0";
+  if (p->smooth_passes > 2) return "smooth_passes above 2 is not supported";
   if (p->q_power != 0.0 && !(p->q_radius > 0.0)) return "q_radius must be > 0";
   return nullptr;
 }
@@ -224,13 +228,13 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
     for (int q = 0; q < 3; ++q) o_lbeta[l][q] = pl.take(n * ms);
   }
   long long nc = (long long)lv[nl - 1].n[0] * lv[nl - 1].n[1] * lv[nl - 1].n[2];
-  size_t o_cg[3];
-  for (int q = 0; q < 3; ++q) o_cg[q] = pl.take(nc * ms);
+  size_t o_cg[3];   // r, d and (Ad, x) in double
+  for (int q = 0; q < 3; ++q) o_cg[q] = pl.take((q == 2 ? 2 : 1) * nc * sizeof(double));
   size_t o_part = pl.take(2 * kRedBlocks * sizeof(double));
   size_t o_scal = pl.take(16 * sizeof(double));
   size_t o_max = pl.take(8 * sizeof(unsigned long long));
   size_t o_flags = pl.take(8 * sizeof(int));
-  size_t o_dt = pl.take(sizeof(double));
+  size_t o_dt = pl.take(2 * sizeof(double));   // dt and 1/dt
   size_t o_lim = pl.take(sizeof(int));
   if (c) {
     char* w = c->ws;
@@ -294,7 +298,10 @@ MGLevel<T> mg_level(fvm_ctx* c, int l, T* x, T* b, T* const* beta) {
   L.geo = make_geo(c->prm, c->shp[l]);
   L.x = x;
   L.b = b;
-  for (int q = 0; q < 3; ++q) L.beta[q] = beta[q];
+  for (int q = 0; q < 3; ++q) {
+    L.beta[q] = beta[q];
+    L.w[q] = (T)L.geo.w[q];
+  }
   for (int d = 0; d < 3; ++d) L.f[d] = c->shp[l].f[d];
   return L;
 }
@@ -319,7 +326,7 @@ template <typename T>
 void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
   cudaStream_t s = c->stream;
   if (l == c->nlev - 1) {
-    TIMED(c, FVM_K_COARSE_CG, 1, launch_coarse_cg<T>(Ls[l], (T*)c->cg[0], (T*)c->cg[1], (T*)c->cg[2],
+    TIMED(c, FVM_K_COARSE_CG, 1, launch_coarse_cg<T>(Ls[l], (double*)c->cg[0], (double*)c->cg[1], (double*)c->cg[2],
                                                    coarse_rtol, c->prm.coarse_maxit, s));
     return;
   }
@@ -474,19 +481,11 @@ fvm_status stage(fvm_ctx* c, Fields<R> X, Fields<R> Sn, Fields<R> Y, double* p, 
                  double cb, double xc, int* cyc, double* rel, bool want_rel) {
   cudaStream_t s = c->stream;
   const Geo& g = c->g;
-  // smoothed phase fraction
-  const R* src = X.alpha;
-  int passes = c->prm.smooth_passes;
-  for (int q = 0; q < passes; ++q) {
-    R* dst = ((passes - q) % 2 == 1) ? (R*)c->as : (R*)c->tmp;
-    TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<R>(g, src, dst, s));
-    src = dst;
-  }
-  const R* as = passes > 0 ? (const R*)c->as : X.alpha;
   R* M[3] = {(R*)c->M[0], (R*)c->M[1], (R*)c->M[2]};
   R* us[3] = {(R*)c->us[0], (R*)c->us[1], (R*)c->us[2]};
-  TIMED(c, FVM_K_INTERFACE, 1, launch_interface<R>(g, c->ph, c->tb, X.alpha, as, X.T, (R*)c->kappa,
-                                                M[0], M[1], M[2], s));
+  // smoothed alpha, normals, curvature and Marangoni vector in one kernel
+  TIMED(c, FVM_K_INTERFACE, 1, launch_interface<R>(g, c->ph, c->tb, c->prm.smooth_passes, X.alpha,
+                                                X.T, (R*)c->kappa, M[0], M[1], M[2], s));
   TIMED(c, FVM_K_SCALARS, 1, launch_scalars<R>(g, c->ph, c->tb, X, Sn, Y, c->dt_dev, ca, cb, xc, s));
   TIMED(c, FVM_K_MOMENTUM, 1, launch_momentum<R>(g, c->ph, c->tb, X, (R*)c->kappa, M[0], M[1], M[2],
                                               us[0], us[1], us[2], c->dt_dev, s));

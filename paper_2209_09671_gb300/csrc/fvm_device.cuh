@@ -122,6 +122,54 @@ __device__ __forceinline__ R sigma_of_T(R T, const Phys& ph) {
   return (R)ph.sigma0 + (R)ph.dsdT * (T - (R)ph.T0);
 }
 
+// Material and source constants in the working precision, so that float
+// kernels carry no double arithmetic or conversions.
+template <typename R>
+struct PhysR {
+  R rho[2], mu[2], lam[2], rcp[2];
+  R sigma0, dsdT, T0;
+  R g[3];
+  R eps_a, eps_T, eps_u, eps_n;
+  R L[3];
+  R h, ih;
+};
+
+template <typename R>
+inline PhysR<R> make_physr(const Phys& ph, const Geo& g) {
+  PhysR<R> q;
+  for (int k = 0; k < 2; ++k) {
+    q.rho[k] = (R)ph.rho[k];
+    q.mu[k] = (R)ph.mu[k];
+    q.lam[k] = (R)ph.lam[k];
+    q.rcp[k] = (R)ph.rcp[k];
+  }
+  q.sigma0 = (R)ph.sigma0;
+  q.dsdT = (R)ph.dsdT;
+  q.T0 = (R)ph.T0;
+  for (int d = 0; d < 3; ++d) {
+    q.g[d] = (R)ph.g[d];
+    q.L[d] = (R)ph.L[d];
+  }
+  q.eps_a = (R)ph.eps_a;
+  q.eps_T = (R)ph.eps_T;
+  q.eps_u = (R)ph.eps_u;
+  q.eps_n = (R)ph.eps_n;
+  q.h = (R)g.h;
+  q.ih = (R)g.ih;
+  return q;
+}
+
+template <typename R>
+__device__ __forceinline__ R mixr(R alpha, const R* pair) {
+  R a = clamp01(alpha);
+  return a * pair[1] + (R(1) - a) * pair[0];
+}
+
+template <typename R>
+__device__ __forceinline__ R sigma_r(R T, const PhysR<R>& q) {
+  return q.sigma0 + q.dsdT * (T - q.T0);
+}
+
 // WENO5-JS value at the face right of v0 from cells v0-2 .. v0+2 (left bias),
 // nonlinear weights a_k = d_k / (eps + beta_k)^2, d = (0.1, 0.6, 0.3).
 // In double the weights are combined over a common denominator so that one

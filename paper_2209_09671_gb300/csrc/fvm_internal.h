@@ -20,9 +20,11 @@ struct Geo {
   int n[3];          // cells per axis x, y, z
   int bc[3];         // PER or WALL per axis
   double h;          // cell edge of the finest level (fine kernels)
+  double ih;         // 1 / h
   double hd[3];      // cell edge per axis on this level (multigrid)
+  double w[3];       // 1 / hd^2 (0 for an axis of one cell: no coupling)
   long long sy, sz;  // strides of y and z
-  long long N;       // cell count
+  long long N;       // cell count (< 2^31, checked at create)
 };
 
 // Dirichlet temperature walls (at most one axis carries them).
@@ -60,19 +62,22 @@ struct MGLevel {
   T* x;
   T* b;
   T* beta[3];
+  T w[3];            // 1 / hd^2 in the level's precision (0: no coupling)
   int f[3];          // coarsening factor to the next level
 };
 
 constexpr int kMaxLevels = 24;
+// thread-block tile of the stage kernels (x fastest)
+constexpr int kBX = 32, kBY = 4, kBZ = 4;
 constexpr int kRedBlocks = 1024;   // partial-sum slots of the two-pass reductions
 
 // ----- stage launchers (fvm_stage.cu) --------------------------------------
 template <typename R>
 void launch_smooth(const Geo& g, const R* in, R* out, cudaStream_t s);
+// smoothing (passes 0..2), face normals, curvature and Marangoni vector
 template <typename R>
-void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, const R* alpha,
-                      const R* alpha_s, const R* T, R* kappa, R* M0, R* M1, R* M2,
-                      cudaStream_t s);
+void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, int passes, const R* alpha,
+                      const R* T, R* kappa, R* M0, R* M1, R* M2, cudaStream_t s);
 template <typename R>
 void launch_scalars(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, Fields<R> Sn,
                     Fields<R> Y, const double* dt, double a, double b, double xc_shift,
@@ -121,9 +126,10 @@ template <typename T>
 void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
 template <typename T>
 void launch_beta_coarsen(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
+// CG vectors are double in both precisions (the coarsest level is small)
 template <typename T>
-void launch_coarse_cg(const MGLevel<T>& L, T* r, T* d, T* Ad, double rtol, int maxit,
-                      cudaStream_t s);
+void launch_coarse_cg(const MGLevel<T>& L, double* r, double* d, double* Ad, double rtol,
+                      int maxit, cudaStream_t s);
 // ||b - L x||^2 into *out (double), x, b, beta in precision T
 template <typename T>
 void launch_residual_norm2(const MGLevel<T>& L, double* partial, double* out, cudaStream_t s);

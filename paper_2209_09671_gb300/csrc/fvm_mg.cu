@@ -100,67 +100,61 @@ void launch_zero(T* a, long long n, cudaStream_t s) {
 // operator pieces on a level
 template <typename T>
 struct OpNb {
-  long long lo[3], hi[3];
+  int lo[3], hi[3];
   T blo[3], bhi[3];
 };
 
 template <typename T>
-__device__ __forceinline__ void neighbours(const MGLevel<T>& L, int i, int j, int k, long long c,
+__device__ __forceinline__ void neighbours(const MGLevel<T>& L, int i, int j, int k, int c,
                                            OpNb<T>& nb) {
   const Geo& g = L.geo;
-  int idx[3] = {i, j, k};
+  const int idx[3] = {i, j, k};
+  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    int n = g.n[d];
-    int lo = idx[d] - 1 < 0 ? idx[d] - 1 + n : idx[d] - 1;
-    int hi = idx[d] + 1 >= n ? idx[d] + 1 - n : idx[d] + 1;
-    int m[3] = {i, j, k};
-    m[d] = lo;
-    nb.lo[d] = lin(g, m[0], m[1], m[2]);
-    m[d] = hi;
-    nb.hi[d] = lin(g, m[0], m[1], m[2]);
+    const int n = g.n[d];
+    const int lo = idx[d] == 0 ? c + (n - 1) * st[d] : c - st[d];
+    const int hi = idx[d] == n - 1 ? c - (n - 1) * st[d] : c + st[d];
+    nb.lo[d] = lo;
+    nb.hi[d] = hi;
     nb.blo[d] = L.beta[d][c];
-    nb.bhi[d] = (g.bc[d] == WALL && idx[d] == n - 1) ? T(0) : L.beta[d][nb.hi[d]];
+    nb.bhi[d] = (g.bc[d] == WALL && idx[d] == n - 1) ? T(0) : L.beta[d][hi];
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T apply_L_at(const MGLevel<T>& L, const T* __restrict__ x, long long c,
+template <typename T, typename X>
+__device__ __forceinline__ X apply_L_at(const MGLevel<T>& L, const X* __restrict__ x, int c,
                                         const OpNb<T>& nb) {
   const Geo& g = L.geo;
-  T xc = x[c];
-  T out = T(0);
+  X xc = x[c];
+  X out = X(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (g.n[d] == 1) continue;
-    T w = (T)(1.0 / (g.hd[d] * g.hd[d]));
-    out += (nb.blo[d] * (xc - x[nb.lo[d]]) + nb.bhi[d] * (xc - x[nb.hi[d]])) * w;
+    out += ((X)nb.blo[d] * (xc - x[nb.lo[d]]) + (X)nb.bhi[d] * (xc - x[nb.hi[d]])) * (X)L.w[d];
   }
   return out;
 }
 
 __device__ __forceinline__ void decode_lv(const Geo& g, long long c, int& i, int& j, int& k) {
-  long long q = c / g.n[0];
-  i = (int)(c - q * g.n[0]);
-  k = (int)(q / g.n[1]);
-  j = (int)(q - (long long)k * g.n[1]);
+  const int cc = (int)c;
+  const int q = cc / g.n[0];
+  i = cc - q * g.n[0];
+  k = q / g.n[1];
+  j = q - k * g.n[1];
 }
 
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_gs(MGLevel<T> L, int colour) {
   const Geo& g = L.geo;
-  int hx = (g.n[0] + 1) >> 1;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long rows = (long long)g.n[1] * g.n[2];
-  if (t >= rows * hx) return;
-  long long row = t / hx;
-  int i2 = (int)(t - row * hx);
-  int k = (int)(row / g.n[1]);
-  int j = (int)(row - (long long)k * g.n[1]);
-  int i = 2 * i2 + ((colour + j + k) & 1);
+  const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (j >= g.n[1] || k >= g.n[2]) return;
+  const int i = 2 * i2 + ((colour + j + k) & 1);
   if (i >= g.n[0]) return;
-  long long c = lin(g, i, j, k);
+  const int c = (k * g.n[1] + j) * g.n[0] + i;
   OpNb<T> nb;
   neighbours(L, i, j, k, c, nb);
   T num = L.b[c];
@@ -168,7 +162,7 @@ __global__ void k_gs(MGLevel<T> L, int colour) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (g.n[d] == 1) continue;
-    T w = (T)(1.0 / (g.hd[d] * g.hd[d]));
+    const T w = L.w[d];
     num += (nb.blo[d] * L.x[nb.lo[d]] + nb.bhi[d] * L.x[nb.hi[d]]) * w;
     den += (nb.blo[d] + nb.bhi[d]) * w;
   }
@@ -177,8 +171,10 @@ __global__ void k_gs(MGLevel<T> L, int colour) {
 
 template <typename T>
 void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s) {
-  long long n = (long long)((L.geo.n[0] + 1) / 2) * L.geo.n[1] * L.geo.n[2];
-  k_gs<T><<<grid1d(n, 256), 256, 0, s>>>(L, colour);
+  const int hx = (L.geo.n[0] + 1) / 2;
+  dim3 bs(32, 4, 2);
+  dim3 gs((hx + 31) / 32, (L.geo.n[1] + 3) / 4, (L.geo.n[2] + 1) / 2);
+  k_gs<T><<<gs, bs, 0, s>>>(L, colour);
 }
 
 // coarse b = mean over children of (b - L x) on the fine level; coarse x = 0
@@ -194,10 +190,10 @@ __global__ void k_residual_restrict(MGLevel<T> F, MGLevel<T> C) {
     for (int dy = 0; dy < F.f[1]; ++dy)
       for (int dx = 0; dx < F.f[0]; ++dx) {
         int i = I * F.f[0] + dx, j = J * F.f[1] + dy, k = K * F.f[2] + dz;
-        long long c = lin(F.geo, i, j, k);
+        const int c = (k * F.geo.n[1] + j) * F.geo.n[0] + i;
         OpNb<T> nb;
         neighbours(F, i, j, k, c, nb);
-        acc += F.b[c] - apply_L_at(F, F.x, c, nb);
+        acc += F.b[c] - apply_L_at<T, T>(F, F.x, c, nb);
         ++cnt;
       }
   C.b[cc] = acc / (T)cnt;
@@ -251,67 +247,71 @@ void launch_beta_coarsen(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t 
 
 // ---------------------------------------------------------------------------
 // conjugate gradients on the coarsest level in one CTA: mean-free rhs,
-// x0 = 0, stop at ||r|| <= rtol ||b||, mean-free result
+// x0 = 0, stop at ||r|| <= rtol ||b|| or on breakdown, mean-free result.
+// The vectors are double in both precisions.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, T* __restrict__ r,
-                                                    T* __restrict__ dd, T* __restrict__ Ad,
-                                                    double rtol, int maxit) {
+__global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, double* __restrict__ r,
+                                                    double* __restrict__ dd,
+                                                    double* __restrict__ Ad, double rtol,
+                                                    int maxit) {
   __shared__ double sh[33];
   const Geo& g = L.geo;
-  const long long N = g.N;
+  const int N = (int)g.N;
   double acc = 0.0;
-  for (long long c = threadIdx.x; c < N; c += blockDim.x) acc += (double)L.b[c];
+  for (int c = threadIdx.x; c < N; c += blockDim.x) acc += (double)L.b[c];
   double mean = block_sum_all(acc, sh) / (double)N;
   acc = 0.0;
-  for (long long c = threadIdx.x; c < N; c += blockDim.x) {
-    T v = (T)((double)L.b[c] - mean);
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    double v = (double)L.b[c] - mean;
     r[c] = v;
     dd[c] = v;
-    L.x[c] = T(0);
-    acc += (double)v * (double)v;
+    Ad[c] = 0.0;      // Ad doubles as the solution accumulator x until the end
+    acc += v * v;
   }
   double rr = block_sum_all(acc, sh);
   double bn = sqrt(rr);
-  if (bn == 0.0) return;
-  for (int it = 0; it < maxit; ++it) {
-    if (sqrt(rr) <= rtol * bn) break;
-    __syncthreads();
-    acc = 0.0;
-    for (long long c = threadIdx.x; c < N; c += blockDim.x) {
-      int i, j, k;
-      decode_lv(g, c, i, j, k);
-      OpNb<T> nb;
-      neighbours(L, i, j, k, c, nb);
-      T a = apply_L_at(L, dd, c, nb);
-      Ad[c] = a;
-      acc += (double)dd[c] * (double)a;
+  double* x = Ad + N;
+  for (int c = threadIdx.x; c < N; c += blockDim.x) x[c] = 0.0;
+  if (bn != 0.0) {
+    for (int it = 0; it < maxit; ++it) {
+      if (sqrt(rr) <= rtol * bn) break;
+      __syncthreads();
+      acc = 0.0;
+      for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        int i, j, k;
+        decode_lv(g, c, i, j, k);
+        OpNb<T> nb;
+        neighbours(L, i, j, k, c, nb);
+        double a = apply_L_at<T, double>(L, dd, c, nb);
+        Ad[c] = a;
+        acc += dd[c] * a;
+      }
+      double pAp = block_sum_all(acc, sh);
+      if (!(pAp > 0.0)) break;   // breakdown (exhausted search direction or rounding)
+      double a = rr / pAp;
+      acc = 0.0;
+      for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        x[c] = x[c] + a * dd[c];
+        double rv = r[c] - a * Ad[c];
+        r[c] = rv;
+        acc += rv * rv;
+      }
+      double rr_new = block_sum_all(acc, sh);
+      double beta = rr_new / rr;
+      for (int c = threadIdx.x; c < N; c += blockDim.x) dd[c] = r[c] + beta * dd[c];
+      rr = rr_new;
     }
-    double pAp = block_sum_all(acc, sh);
-    if (!(pAp > 0.0)) break;   // breakdown (exhausted search direction or rounding)
-    double a = rr / pAp;
-    acc = 0.0;
-    for (long long c = threadIdx.x; c < N; c += blockDim.x) {
-      L.x[c] = (T)((double)L.x[c] + a * (double)dd[c]);
-      T rv = (T)((double)r[c] - a * (double)Ad[c]);
-      r[c] = rv;
-      acc += (double)rv * (double)rv;
-    }
-    double rr_new = block_sum_all(acc, sh);
-    double beta = rr_new / rr;
-    for (long long c = threadIdx.x; c < N; c += blockDim.x)
-      dd[c] = (T)((double)r[c] + beta * (double)dd[c]);
-    rr = rr_new;
   }
   __syncthreads();
   acc = 0.0;
-  for (long long c = threadIdx.x; c < N; c += blockDim.x) acc += (double)L.x[c];
+  for (int c = threadIdx.x; c < N; c += blockDim.x) acc += x[c];
   double xm = block_sum_all(acc, sh) / (double)N;
-  for (long long c = threadIdx.x; c < N; c += blockDim.x) L.x[c] = (T)((double)L.x[c] - xm);
+  for (int c = threadIdx.x; c < N; c += blockDim.x) L.x[c] = (T)(x[c] - xm);
 }
 
 template <typename T>
-void launch_coarse_cg(const MGLevel<T>& L, T* r, T* d, T* Ad, double rtol, int maxit,
-                      cudaStream_t s) {
+void launch_coarse_cg(const MGLevel<T>& L, double* r, double* d, double* Ad, double rtol,
+                      int maxit, cudaStream_t s) {
   k_coarse_cg<T><<<1, 1024, 0, s>>>(L, r, d, Ad, rtol, maxit);
 }
 
@@ -325,8 +325,8 @@ __global__ void k_residual_norm2(MGLevel<T> L, double* __restrict__ partial) {
     int i, j, k;
     decode_lv(L.geo, c, i, j, k);
     OpNb<T> nb;
-    neighbours(L, i, j, k, c, nb);
-    double r = (double)(L.b[c] - apply_L_at(L, L.x, c, nb));
+    neighbours(L, i, j, k, (int)c, nb);
+    double r = (double)(L.b[c] - apply_L_at<T, T>(L, L.x, (int)c, nb));
     acc += r * r;
   }
   double s = block_sum_all(acc, sh);
@@ -345,31 +345,27 @@ __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* 
                              double* __restrict__ partial) {
   __shared__ double sh[33];
   const float* be[3] = {b0, b1, b2};
+  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
   double acc = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
-       c += (long long)gridDim.x * blockDim.x) {
+  for (long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x; cl < g.N;
+       cl += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)cl;
     int i, j, k;
     decode_lv(g, c, i, j, k);
-    int idx[3] = {i, j, k};
-    double pc = p[c];
+    const int idx[3] = {i, j, k};
+    const double pc = p[c];
     double Lp = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      int n = g.n[d];
+      const int n = g.n[d];
       if (n == 1) continue;
-      int lo = idx[d] - 1 < 0 ? idx[d] - 1 + n : idx[d] - 1;
-      int hi = idx[d] + 1 >= n ? idx[d] + 1 - n : idx[d] + 1;
-      int m[3] = {i, j, k};
-      m[d] = lo;
-      long long clo = lin(g, m[0], m[1], m[2]);
-      m[d] = hi;
-      long long chi = lin(g, m[0], m[1], m[2]);
-      double blo = (double)be[d][c];
-      double bhi = (g.bc[d] == WALL && idx[d] == n - 1) ? 0.0 : (double)be[d][chi];
-      double w = 1.0 / (g.hd[d] * g.hd[d]);
-      Lp += (blo * (pc - p[clo]) + bhi * (pc - p[chi])) * w;
+      const int clo = idx[d] == 0 ? c + (n - 1) * st[d] : c - st[d];
+      const int chi = idx[d] == n - 1 ? c - (n - 1) * st[d] : c + st[d];
+      const double blo = (double)be[d][c];
+      const double bhi = (g.bc[d] == WALL && idx[d] == n - 1) ? 0.0 : (double)be[d][chi];
+      Lp += (blo * (pc - p[clo]) + bhi * (pc - p[chi])) * g.w[d];
     }
-    double r = b[c] - Lp;
+    const double r = b[c] - Lp;
     r32[c] = (float)r;
     acc += r * r;
   }
@@ -401,8 +397,8 @@ void launch_add_correction(long long n, double* p, const float* e, cudaStream_t 
                                             cudaStream_t);                                   \
   template void launch_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);       \
   template void launch_beta_coarsen<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);  \
-  template void launch_coarse_cg<T>(const MGLevel<T>&, T*, T*, T*, double, int,              \
-                                    cudaStream_t);                                           \
+  template void launch_coarse_cg<T>(const MGLevel<T>&, double*, double*, double*, double,  \
+                                    int, cudaStream_t);                                      \
   template void launch_residual_norm2<T>(const MGLevel<T>&, double*, double*, cudaStream_t);
 
 FVM_MG_INST(double)

@@ -15,17 +15,30 @@
 //   k_correct     u = u* - dt beta grad p and the RK combination
 //   k_dt_reduce   maxima for the time-step limits; k_dt_final combines them
 //   k_diagnostics volume / mass sums, max |D u| dt, NaN flag
+//
+// Layout of the work: a CTA owns a kBX x kBY x kBZ tile of cells on a 3D grid.
+// Every face flux (and every edge flux of the momentum control volumes) is
+// evaluated once, by the thread owning the face, and exchanged through shared
+// memory; the threads on the high (or low) side of the tile evaluate the one
+// extra layer the divergence needs.  Tiles whose stencil reach (3 cells)
+// stays inside the domain take loads without boundary handling; the others
+// go through the wrap/mirror loaders.
 #include "fvm_device.cuh"
 
 namespace fvm {
 
 static inline unsigned grid1d(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+static inline dim3 tile_grid(const Geo& g) {
+  return dim3((unsigned)((g.n[0] + kBX - 1) / kBX), (unsigned)((g.n[1] + kBY - 1) / kBY),
+              (unsigned)((g.n[2] + kBZ - 1) / kBZ));
+}
 
 __device__ __forceinline__ void decode(const Geo& g, long long c, int& i, int& j, int& k) {
-  long long q = c / g.n[0];
-  i = (int)(c - q * g.n[0]);
-  k = (int)(q / g.n[1]);
-  j = (int)(q - (long long)k * g.n[1]);
+  int cc = (int)c;
+  int q = cc / g.n[0];
+  i = cc - q * g.n[0];
+  k = q / g.n[1];
+  j = q - k * g.n[1];
 }
 
 template <int D>
@@ -35,104 +48,269 @@ __device__ __forceinline__ void shift(int& i, int& j, int& k, int s) {
   if (D == 2) k += s;
 }
 
+// loads with (IN = false) or without (IN = true) boundary handling
+template <bool IN>
+struct Ld {
+  template <typename R>
+  static __device__ __forceinline__ R even(const R* __restrict__ a, const Geo& g, int i, int j,
+                                           int k) {
+    if (IN) return __ldg(a + ((k * (int)g.n[1] + j) * (int)g.n[0] + i));
+    return ld_even(a, g, i, j, k);
+  }
+  template <int C, typename R>
+  static __device__ __forceinline__ R vel(const R* __restrict__ a, const Geo& g, int i, int j,
+                                          int k) {
+    if (IN) return __ldg(a + ((k * (int)g.n[1] + j) * (int)g.n[0] + i));
+    return ld_vel<C>(a, g, i, j, k);
+  }
+  template <typename R>
+  static __device__ __forceinline__ R T(const R* __restrict__ a, const Geo& g, const TBC& tb,
+                                        int i, int j, int k) {
+    if (IN) return __ldg(a + ((k * (int)g.n[1] + j) * (int)g.n[0] + i));
+    return ld_T(a, g, tb, i, j, k);
+  }
+};
+
+// the tile and its stencil reach H stay inside the domain on every axis
+__device__ __forceinline__ bool tile_interior(const Geo& g, int H) {
+  const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * kBZ;
+  return x0 - H >= 0 && x0 + kBX - 1 + H < g.n[0] && y0 - H >= 0 &&
+         y0 + kBY - 1 + H < g.n[1] && z0 - H >= 0 && z0 + kBZ - 1 + H < g.n[2];
+}
+
 // ---------------------------------------------------------------------------
 // smoothing: one pass of the separable [1,2,1]/4 filter in all axes with
 // more than one cell, as a 27-point tensor product
-template <typename R>
-__global__ void k_smooth(Geo g, const R* __restrict__ in, R* __restrict__ out) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  int i, j, k;
-  decode(g, c, i, j, k);
-  int lo[3], hi[3];
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = g.n[d] > 1 ? -1 : 0;
-    hi[d] = g.n[d] > 1 ? 1 : 0;
-  }
+template <bool IN, typename R>
+__device__ __forceinline__ void smooth_body(const Geo& g, const R* __restrict__ in,
+                                            R* __restrict__ out, int i, int j, int k) {
+  const int lo0 = g.n[0] > 1 ? -1 : 0, lo1 = g.n[1] > 1 ? -1 : 0, lo2 = g.n[2] > 1 ? -1 : 0;
   R acc = 0;
-  for (int dz = lo[2]; dz <= hi[2]; ++dz) {
-    R wz = g.n[2] > 1 ? (dz == 0 ? R(0.5) : R(0.25)) : R(1);
+  for (int dz = lo2; dz <= -lo2; ++dz) {
+    R wz = lo2 ? (dz == 0 ? R(0.5) : R(0.25)) : R(1);
     R accy = 0;
-    for (int dy = lo[1]; dy <= hi[1]; ++dy) {
-      R wy = g.n[1] > 1 ? (dy == 0 ? R(0.5) : R(0.25)) : R(1);
+    for (int dy = lo1; dy <= -lo1; ++dy) {
+      R wy = lo1 ? (dy == 0 ? R(0.5) : R(0.25)) : R(1);
       R accx = 0;
-      for (int dx = lo[0]; dx <= hi[0]; ++dx) {
-        R wx = g.n[0] > 1 ? (dx == 0 ? R(0.5) : R(0.25)) : R(1);
-        accx += wx * ld_even(in, g, i + dx, j + dy, k + dz);
+      for (int dx = lo0; dx <= -lo0; ++dx) {
+        R wx = lo0 ? (dx == 0 ? R(0.5) : R(0.25)) : R(1);
+        accx += wx * Ld<IN>::even(in, g, i + dx, j + dy, k + dz);
       }
       accy += wy * accx;
     }
     acc += wz * accy;
   }
-  out[c] = acc;
+  out[(k * g.n[1] + j) * g.n[0] + i] = acc;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBX * kBY * kBZ) k_smooth(Geo g, const R* __restrict__ in,
+                                                            R* __restrict__ out) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y,
+            k = blockIdx.z * kBZ + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  if (tile_interior(g, 1)) smooth_body<true>(g, in, out, i, j, k);
+  else smooth_body<false>(g, in, out, i, j, k);
 }
 
 template <typename R>
 void launch_smooth(const Geo& g, const R* in, R* out, cudaStream_t s) {
-  k_smooth<R><<<grid1d(g.N, 256), 256, 0, s>>>(g, in, out);
+  k_smooth<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), 0, s>>>(g, in, out);
 }
 
 // ---------------------------------------------------------------------------
-// interface geometry
-template <typename R>
-__device__ __forceinline__ R at_s(const R* a, const Geo& g, int i, int j, int k) {
-  return ld_even(a, g, i, j, k);
+// shared-memory tiles: a field staged with a halo of H cells around the CTA's
+// tile; local coordinates run from -H to kB*+H-1
+constexpr int kThreads = kBX * kBY * kBZ;
+
+template <int H>
+struct Tile {
+  static constexpr int SX = kBX + 2 * H, SY = kBY + 2 * H, SZ = kBZ + 2 * H;
+  static constexpr int N = SX * SY * SZ;
+  static __device__ __forceinline__ int at(int lx, int ly, int lz) {
+    return ((lz + H) * SY + (ly + H)) * SX + (lx + H);
+  }
+};
+
+__device__ __forceinline__ int flat_tid() {
+  return threadIdx.x + kBX * (threadIdx.y + kBY * threadIdx.z);
 }
 
-// n_D on the low D-face of cell (i,j,k) + s e_D, from the smoothed alpha
+enum { F_EVEN = 0, F_VEL = 1, F_TEMP = 2 };
+
+// stage one field into s: the boundary rules of the loaders are applied once
+// per staged point; points more than H cells outside the domain (ragged
+// tiles) are never read and hold 0
+template <int H, int KIND, int C, typename R>
+__device__ __forceinline__ void stage(R* __restrict__ s, const R* __restrict__ a, const Geo& g,
+                                      const TBC& tb) {
+  const bool in = tile_interior(g, H);
+  const int x0 = blockIdx.x * kBX - H, y0 = blockIdx.y * kBY - H, z0 = blockIdx.z * kBZ - H;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  for (int e = flat_tid(); e < Tile<H>::N; e += kThreads) {
+    const int lx = e % Tile<H>::SX;
+    const int t = e / Tile<H>::SX;
+    const int ly = t % Tile<H>::SY;
+    const int lz = t / Tile<H>::SY;
+    const int i = x0 + lx, j = y0 + ly, k = z0 + lz;
+    R v;
+    if (in) {
+      v = __ldg(a + ((k * ny + j) * nx + i));
+    } else if (i < -H || i > nx - 1 + H || j < -H || j > ny - 1 + H || k < -H || k > nz - 1 + H) {
+      v = R(0);
+    } else if (KIND == F_EVEN) {
+      v = ld_even(a, g, i, j, k);
+    } else if (KIND == F_VEL) {
+      v = ld_vel<C>(a, g, i, j, k);
+    } else {
+      v = ld_T(a, g, tb, i, j, k);
+    }
+    s[e] = v;
+  }
+}
+
+template <int A>
+__device__ __forceinline__ int tsel(int tx, int ty, int tz) {
+  return A == 0 ? tx : (A == 1 ? ty : tz);
+}
+
+// ---------------------------------------------------------------------------
+// interface geometry: two smoothing passes, face normals, curvature and the
+// Marangoni vector in one kernel (the smoothed alpha never leaves the SM)
+template <typename R>
+struct IfaceShared {
+  R a[Tile<3>::N];          // alpha
+  R s1[Tile<2>::N];         // after the first [1,2,1]/4 pass
+  R s2[Tile<1>::N];         // smoothed alpha
+  R T[Tile<1>::N];
+  R nx[kBZ][kBY][kBX + 1];  // face normals
+  R ny[kBZ][kBY + 1][kBX];
+  R nz[kBZ + 1][kBY][kBX];
+};
+
+// one [1,2,1]/4 tensor pass from a tile of halo HI onto the tile of halo HO
+template <int HI, int HO, typename R>
+__device__ __forceinline__ void smooth_pass(const Geo& g, const R* __restrict__ in,
+                                            R* __restrict__ out) {
+  const bool sx = g.n[0] > 1, sy = g.n[1] > 1, sz = g.n[2] > 1;
+  for (int e = flat_tid(); e < Tile<HO>::N; e += kThreads) {
+    const int lx = e % Tile<HO>::SX - HO;
+    const int t = e / Tile<HO>::SX;
+    const int ly = t % Tile<HO>::SY - HO;
+    const int lz = t / Tile<HO>::SY - HO;
+    R acc = 0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      if (!sz && dz != 0) continue;
+      const R wz = sz ? (dz == 0 ? R(0.5) : R(0.25)) : R(1);
+      R accy = 0;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        if (!sy && dy != 0) continue;
+        const R wy = sy ? (dy == 0 ? R(0.5) : R(0.25)) : R(1);
+        R accx = 0;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (!sx && dx != 0) continue;
+          const R wx = sx ? (dx == 0 ? R(0.5) : R(0.25)) : R(1);
+          accx += wx * in[Tile<HI>::at(lx + dx, ly + dy, lz + dz)];
+        }
+        accy += wy * accx;
+      }
+      acc += wz * accy;
+    }
+    out[e] = acc;
+  }
+}
+
+template <int HI, int HO, typename R>
+__device__ __forceinline__ void copy_tile(const R* __restrict__ in, R* __restrict__ out) {
+  for (int e = flat_tid(); e < Tile<HO>::N; e += kThreads) {
+    const int lx = e % Tile<HO>::SX - HO;
+    const int t = e / Tile<HO>::SX;
+    const int ly = t % Tile<HO>::SY - HO;
+    const int lz = t / Tile<HO>::SY - HO;
+    out[e] = in[Tile<HI>::at(lx, ly, lz)];
+  }
+}
+
+// n_D on the low D-face of local cell (lx,ly,lz), from the smoothed alpha:
+// grad / (|grad| + eps_n) with the normal derivative across the face and each
+// tangential derivative the mean of the two cells' central differences
 template <int D, typename R>
-__device__ __forceinline__ R face_normal(const R* __restrict__ as, const Geo& g, int i, int j,
-                                         int k, int s, R ih, R epsn) {
-  int i1 = i, j1 = j, k1 = k, i0 = i, j0 = j, k0 = k;
-  shift<D>(i1, j1, k1, s);
-  shift<D>(i0, j0, k0, s - 1);
-  R gd = (at_s(as, g, i1, j1, k1) - at_s(as, g, i0, j0, k0)) * ih;
+__device__ __forceinline__ R face_normal(const R* __restrict__ s2, int lx, int ly, int lz, R ih,
+                                         R epsn) {
+  const int dx = D == 0, dy = D == 1, dz = D == 2;
+  R gd = (s2[Tile<1>::at(lx, ly, lz)] - s2[Tile<1>::at(lx - dx, ly - dy, lz - dz)]) * ih;
   R sq = gd * gd;
   const R q = ih * R(0.25);
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
     if (t == D) continue;
-    int a1 = i1, b1 = j1, c1 = k1, a2 = i1, b2 = j1, c2 = k1;
-    int a3 = i0, b3 = j0, c3 = k0, a4 = i0, b4 = j0, c4 = k0;
-    if (t == 0) { a1 += 1; a2 -= 1; a3 += 1; a4 -= 1; }
-    if (t == 1) { b1 += 1; b2 -= 1; b3 += 1; b4 -= 1; }
-    if (t == 2) { c1 += 1; c2 -= 1; c3 += 1; c4 -= 1; }
-    R gt = ((at_s(as, g, a1, b1, c1) - at_s(as, g, a2, b2, c2)) +
-            (at_s(as, g, a3, b3, c3) - at_s(as, g, a4, b4, c4))) * q;
+    const int ox = t == 0, oy = t == 1, oz = t == 2;
+    R gt = ((s2[Tile<1>::at(lx + ox, ly + oy, lz + oz)] - s2[Tile<1>::at(lx - ox, ly - oy, lz - oz)]) +
+            (s2[Tile<1>::at(lx - dx + ox, ly - dy + oy, lz - dz + oz)] -
+             s2[Tile<1>::at(lx - dx - ox, ly - dy - oy, lz - dz - oz)])) * q;
     sq += gt * gt;
   }
   return gd / (sqrt(sq) + epsn);
 }
 
 template <typename R>
-__global__ void k_interface(Geo g, Phys ph, TBC tb, const R* __restrict__ alpha,
-                            const R* __restrict__ as, const R* __restrict__ T,
-                            R* __restrict__ kappa, R* __restrict__ M0, R* __restrict__ M1,
-                            R* __restrict__ M2) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  int i, j, k;
-  decode(g, c, i, j, k);
-  const R ih = R(1.0 / g.h);
-  const R epsn = (R)ph.eps_n;
+__global__ void __launch_bounds__(kThreads)
+    k_interface(Geo g, PhysR<R> ph, TBC tb, int passes, const R* __restrict__ alpha,
+                const R* __restrict__ T, R* __restrict__ kappa, R* __restrict__ M0,
+                R* __restrict__ M1, R* __restrict__ M2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  IfaceShared<R>& S = *reinterpret_cast<IfaceShared<R>*>(smem_raw);
+  stage<3, F_EVEN, 0>(S.a, alpha, g, tb);
+  stage<1, F_TEMP, 0>(S.T, T, g, tb);
+  __syncthreads();
+  if (passes >= 1) {
+    smooth_pass<3, 2>(g, S.a, S.s1);
+    __syncthreads();
+    if (passes >= 2) smooth_pass<2, 1>(g, S.s1, S.s2);
+    else copy_tile<2, 1>(S.s1, S.s2);
+  } else {
+    copy_tile<3, 1>(S.a, S.s2);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const R ih = ph.ih;
+  const R epsn = ph.eps_n;
+  if (i <= nx && j < ny && k < nz) {
+    S.nx[tz][ty][tx] = face_normal<0>(S.s2, tx, ty, tz, ih, epsn);
+    if (tx == kBX - 1 && i + 1 <= nx) S.nx[tz][ty][tx + 1] = face_normal<0>(S.s2, tx + 1, ty, tz, ih, epsn);
+  }
+  if (i < nx && j <= ny && k < nz) {
+    S.ny[tz][ty][tx] = face_normal<1>(S.s2, tx, ty, tz, ih, epsn);
+    if (ty == kBY - 1 && j + 1 <= ny) S.ny[tz][ty + 1][tx] = face_normal<1>(S.s2, tx, ty + 1, tz, ih, epsn);
+  }
+  if (i < nx && j < ny && k <= nz) {
+    S.nz[tz][ty][tx] = face_normal<2>(S.s2, tx, ty, tz, ih, epsn);
+    if (tz == kBZ - 1 && k + 1 <= nz) S.nz[tz + 1][ty][tx] = face_normal<2>(S.s2, tx, ty, tz + 1, ih, epsn);
+  }
+  __syncthreads();
+  if (i >= nx || j >= ny || k >= nz) return;
+  const int c = (k * ny + j) * nx + i;
   R kap = 0;
-  kap += (face_normal<0>(as, g, i, j, k, 1, ih, epsn) - face_normal<0>(as, g, i, j, k, 0, ih, epsn)) * ih;
-  kap += (face_normal<1>(as, g, i, j, k, 1, ih, epsn) - face_normal<1>(as, g, i, j, k, 0, ih, epsn)) * ih;
-  kap += (face_normal<2>(as, g, i, j, k, 1, ih, epsn) - face_normal<2>(as, g, i, j, k, 0, ih, epsn)) * ih;
+  kap += (S.nx[tz][ty][tx + 1] - S.nx[tz][ty][tx]) * ih;
+  kap += (S.ny[tz][ty + 1][tx] - S.ny[tz][ty][tx]) * ih;
+  kap += (S.nz[tz + 1][ty][tx] - S.nz[tz][ty][tx]) * ih;
   kappa[c] = kap;
-
-  // Marangoni vector from central differences
+  // Marangoni vector from central differences of alpha, smoothed alpha, sigma(T)
   const R i2h = R(0.5) * ih;
   R gv[3], tv[3], sv[3];
-  gv[0] = (ld_even(alpha, g, i + 1, j, k) - ld_even(alpha, g, i - 1, j, k)) * i2h;
-  gv[1] = (ld_even(alpha, g, i, j + 1, k) - ld_even(alpha, g, i, j - 1, k)) * i2h;
-  gv[2] = (ld_even(alpha, g, i, j, k + 1) - ld_even(alpha, g, i, j, k - 1)) * i2h;
-  tv[0] = (ld_even(as, g, i + 1, j, k) - ld_even(as, g, i - 1, j, k)) * i2h;
-  tv[1] = (ld_even(as, g, i, j + 1, k) - ld_even(as, g, i, j - 1, k)) * i2h;
-  tv[2] = (ld_even(as, g, i, j, k + 1) - ld_even(as, g, i, j, k - 1)) * i2h;
-  sv[0] = (sigma_of_T(ld_T(T, g, tb, i + 1, j, k), ph) - sigma_of_T(ld_T(T, g, tb, i - 1, j, k), ph)) * i2h;
-  sv[1] = (sigma_of_T(ld_T(T, g, tb, i, j + 1, k), ph) - sigma_of_T(ld_T(T, g, tb, i, j - 1, k), ph)) * i2h;
-  sv[2] = (sigma_of_T(ld_T(T, g, tb, i, j, k + 1), ph) - sigma_of_T(ld_T(T, g, tb, i, j, k - 1), ph)) * i2h;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int ox = d == 0, oy = d == 1, oz = d == 2;
+    gv[d] = (S.a[Tile<3>::at(tx + ox, ty + oy, tz + oz)] - S.a[Tile<3>::at(tx - ox, ty - oy, tz - oz)]) * i2h;
+    tv[d] = (S.s2[Tile<1>::at(tx + ox, ty + oy, tz + oz)] - S.s2[Tile<1>::at(tx - ox, ty - oy, tz - oz)]) * i2h;
+    sv[d] = (sigma_r(S.T[Tile<1>::at(tx + ox, ty + oy, tz + oz)], ph) -
+             sigma_r(S.T[Tile<1>::at(tx - ox, ty - oy, tz - oz)], ph)) * i2h;
+  }
   R gn = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
   R tn = sqrt(tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]) + epsn;
   R n0 = tv[0] / tn, n1 = tv[1] / tn, n2 = tv[2] / tn;
@@ -143,73 +321,120 @@ __global__ void k_interface(Geo g, Phys ph, TBC tb, const R* __restrict__ alpha,
 }
 
 template <typename R>
-void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, const R* alpha,
-                      const R* alpha_s, const R* T, R* kappa, R* M0, R* M1, R* M2,
-                      cudaStream_t s) {
-  k_interface<R><<<grid1d(g.N, 128), 128, 0, s>>>(g, ph, tb, alpha, alpha_s, T, kappa, M0, M1, M2);
+void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, int passes, const R* alpha,
+                      const R* T, R* kappa, R* M0, R* M1, R* M2, cudaStream_t s) {
+  const int smem = (int)sizeof(IfaceShared<R>);
+  cudaFuncSetAttribute(k_interface<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_interface<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
+      g, make_physr<R>(ph, g), tb, passes, alpha, T, kappa, M0, M1, M2);
 }
 
 // ---------------------------------------------------------------------------
 // scalar transport (alpha, T) and stage update
+
+// face fluxes of one tile: [0] alpha advection, [1] T advection, [2] T conduction
+template <typename R>
+struct ScalFlux {
+  R x[3][kBZ][kBY][kBX + 1];
+  R y[3][kBZ][kBY + 1][kBX];
+  R z[3][kBZ + 1][kBY][kBX];
+};
+
+template <typename R>
+struct ScalShared {
+  R a[Tile<3>::N];
+  R T[Tile<3>::N];
+  R u[3][Tile<1>::N];
+  ScalFlux<R> F;
+};
+
+// advective fluxes of alpha and T and the conductive flux of T through the
+// low D-face of local cell (lx,ly,lz)
 template <int D, typename R>
-__device__ __forceinline__ void scalar_axis(const Geo& g, const Phys& ph, const TBC& tb,
-                                            const Fields<R>& X, int i, int j, int k, R ih,
-                                            R& Ra, R& RT, R& Dif, R& gcomp) {
-  R av[7], tv[7];
+__device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<R>& ph, int lx,
+                                            int ly, int lz, R& Fa, R& FT, R& Df) {
+  const int dx = D == 0, dy = D == 1, dz = D == 2;
+  R av[6], tv[6];
 #pragma unroll
-  for (int m = 0; m < 7; ++m) {
-    int a = i, b = j, c = k;
-    shift<D>(a, b, c, m - 3);
-    av[m] = ld_even(X.alpha, g, a, b, c);
-    tv[m] = ld_T(X.T, g, tb, a, b, c);
+  for (int m = 0; m < 6; ++m) {
+    const int o = m - 3;
+    av[m] = S.a[Tile<3>::at(lx + o * dx, ly + o * dy, lz + o * dz)];
+    tv[m] = S.T[Tile<3>::at(lx + o * dx, ly + o * dy, lz + o * dz)];
   }
-  const R* U = X.u[D];
-  R Fa[2], FT[2], Df[2];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    int a = i, b = j, c = k;
-    shift<D>(a, b, c, s);
-    R Uf = ld_vel<D>(U, g, a, b, c);
-    Fa[s] = upwind_flux(Uf, av + s, (R)ph.eps_a);
-    FT[s] = upwind_flux(Uf, tv + s, (R)ph.eps_T);
-    R lL = mixp(av[2 + s], ph.lam), lR = mixp(av[3 + s], ph.lam);
-    R lf = R(2) * lL * lR / (lL + lR);
-    Df[s] = lf * (tv[3 + s] - tv[2 + s]) * ih;
-  }
-  Ra -= (Fa[1] - Fa[0]) * ih;
-  RT -= (FT[1] - FT[0]) * ih;
-  Dif += (Df[1] - Df[0]) * ih;
-  gcomp = (av[4] - av[2]) * (R(0.5) * ih);
+  const R Uf = S.u[D][Tile<1>::at(lx, ly, lz)];
+  Fa = upwind_flux(Uf, av, ph.eps_a);
+  FT = upwind_flux(Uf, tv, ph.eps_T);
+  R lL = mixr(av[2], ph.lam), lR = mixr(av[3], ph.lam);
+  R lf = R(2) * lL * lR / (lL + lR);
+  Df = lf * (tv[3] - tv[2]) * ph.ih;
 }
 
 template <typename R>
-__global__ void k_scalars(Geo g, Phys ph, TBC tb, Fields<R> X, Fields<R> Sn, Fields<R> Y,
-                          const double* __restrict__ dtp, R a, R b, double xc) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  int i, j, k;
-  decode(g, c, i, j, k);
-  const R ih = R(1.0 / g.h);
-  const R dt = (R)(*dtp);
-  R Ra = 0, RT = 0, Dif = 0, gx, gy, gz;
-  scalar_axis<0>(g, ph, tb, X, i, j, k, ih, Ra, RT, Dif, gx);
-  scalar_axis<1>(g, ph, tb, X, i, j, k, ih, Ra, RT, Dif, gy);
-  scalar_axis<2>(g, ph, tb, X, i, j, k, ih, Ra, RT, Dif, gz);
-  R al = X.alpha[c];
-  R rcp = mixp(al, ph.rcp);
+__global__ void __launch_bounds__(kThreads)
+    k_scalars(Geo g, PhysR<R> ph, TBC tb, Fields<R> X, Fields<R> Sn, Fields<R> Y,
+              const double* __restrict__ dtp, R a, R b, R xc, R yc, R qamp, R ir2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ScalShared<R>& S = *reinterpret_cast<ScalShared<R>*>(smem_raw);
+  stage<3, F_EVEN, 0>(S.a, X.alpha, g, tb);
+  stage<3, F_TEMP, 0>(S.T, X.T, g, tb);
+  stage<1, F_VEL, 0>(S.u[0], X.u[0], g, tb);
+  stage<1, F_VEL, 1>(S.u[1], X.u[1], g, tb);
+  stage<1, F_VEL, 2>(S.u[2], X.u[2], g, tb);
+  __syncthreads();
+  const R dt = (R)dtp[0];
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const R ih = ph.ih;
+  ScalFlux<R>& F = S.F;
+  if (i <= nx && j < ny && k < nz) {
+    scalar_face<0>(S, ph, tx, ty, tz, F.x[0][tz][ty][tx], F.x[1][tz][ty][tx], F.x[2][tz][ty][tx]);
+    if (tx == kBX - 1 && i + 1 <= nx)
+      scalar_face<0>(S, ph, tx + 1, ty, tz, F.x[0][tz][ty][tx + 1], F.x[1][tz][ty][tx + 1],
+                     F.x[2][tz][ty][tx + 1]);
+  }
+  if (i < nx && j <= ny && k < nz) {
+    scalar_face<1>(S, ph, tx, ty, tz, F.y[0][tz][ty][tx], F.y[1][tz][ty][tx], F.y[2][tz][ty][tx]);
+    if (ty == kBY - 1 && j + 1 <= ny)
+      scalar_face<1>(S, ph, tx, ty + 1, tz, F.y[0][tz][ty + 1][tx], F.y[1][tz][ty + 1][tx],
+                     F.y[2][tz][ty + 1][tx]);
+  }
+  if (i < nx && j < ny && k <= nz) {
+    scalar_face<2>(S, ph, tx, ty, tz, F.z[0][tz][ty][tx], F.z[1][tz][ty][tx], F.z[2][tz][ty][tx]);
+    if (tz == kBZ - 1 && k + 1 <= nz)
+      scalar_face<2>(S, ph, tx, ty, tz + 1, F.z[0][tz + 1][ty][tx], F.z[1][tz + 1][ty][tx],
+                     F.z[2][tz + 1][ty][tx]);
+  }
+  __syncthreads();
+  if (i >= nx || j >= ny || k >= nz) return;
+  const int c = (k * ny + j) * nx + i;
+  R Ra = 0, RT = 0, Dif = 0;
+  Ra -= (F.x[0][tz][ty][tx + 1] - F.x[0][tz][ty][tx]) * ih;
+  RT -= (F.x[1][tz][ty][tx + 1] - F.x[1][tz][ty][tx]) * ih;
+  Dif += (F.x[2][tz][ty][tx + 1] - F.x[2][tz][ty][tx]) * ih;
+  Ra -= (F.y[0][tz][ty + 1][tx] - F.y[0][tz][ty][tx]) * ih;
+  RT -= (F.y[1][tz][ty + 1][tx] - F.y[1][tz][ty][tx]) * ih;
+  Dif += (F.y[2][tz][ty + 1][tx] - F.y[2][tz][ty][tx]) * ih;
+  Ra -= (F.z[0][tz + 1][ty][tx] - F.z[0][tz][ty][tx]) * ih;
+  RT -= (F.z[1][tz + 1][ty][tx] - F.z[1][tz][ty][tx]) * ih;
+  Dif += (F.z[2][tz + 1][ty][tx] - F.z[2][tz][ty][tx]) * ih;
+  const R al = S.a[Tile<3>::at(tx, ty, tz)];
+  const R rcp = mixr(al, ph.rcp);
   RT += Dif / rcp;
-  if (ph.q_power != 0.0) {
-    double x = (i + 0.5) * g.h, y = (j + 0.5) * g.h;
-    double dx = x - xc, dy = y - ph.q_y0;
-    if (g.bc[0] == PER) dx = dx - ph.L[0] * floor(dx / ph.L[0] + 0.5);
-    if (g.bc[1] == PER) dy = dy - ph.L[1] * floor(dy / ph.L[1] + 0.5);
-    double r2 = ph.q_radius * ph.q_radius;
-    double q = 2.0 * ph.q_power / (M_PI * r2) * exp(-2.0 * (dx * dx + dy * dy) / r2);
+  if (qamp != R(0)) {
+    const R i2h = R(0.5) * ih;
+    R gx = (S.a[Tile<3>::at(tx + 1, ty, tz)] - S.a[Tile<3>::at(tx - 1, ty, tz)]) * i2h;
+    R gy = (S.a[Tile<3>::at(tx, ty + 1, tz)] - S.a[Tile<3>::at(tx, ty - 1, tz)]) * i2h;
+    R gz = (S.a[Tile<3>::at(tx, ty, tz + 1)] - S.a[Tile<3>::at(tx, ty, tz - 1)]) * i2h;
+    R dx = (R(i) + R(0.5)) * ph.h - xc, dy = (R(j) + R(0.5)) * ph.h - yc;
+    if (g.bc[0] == PER) dx = dx - ph.L[0] * floor(dx / ph.L[0] + R(0.5));
+    if (g.bc[1] == PER) dy = dy - ph.L[1] * floor(dy / ph.L[1] + R(0.5));
+    R q = qamp * exp(R(-2) * (dx * dx + dy * dy) * ir2);
     R gn = sqrt(gx * gx + gy * gy + gz * gz);
-    RT += (R)q * gn / rcp;
+    RT += q * gn / rcp;
   }
   R Ea = al + dt * Ra;
-  R ET = X.T[c] + dt * RT;
+  R ET = S.T[Tile<3>::at(tx, ty, tz)] + dt * RT;
   Y.alpha[c] = a * Sn.alpha[c] + b * Ea;
   Y.T[c] = a * Sn.T[c] + b * ET;
 }
@@ -217,132 +442,216 @@ __global__ void k_scalars(Geo g, Phys ph, TBC tb, Fields<R> X, Fields<R> Sn, Fie
 template <typename R>
 void launch_scalars(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, Fields<R> Sn,
                     Fields<R> Y, const double* dt, double a, double b, double xc, cudaStream_t s) {
-  k_scalars<R><<<grid1d(g.N, 128), 128, 0, s>>>(g, ph, tb, X, Sn, Y, dt, (R)a, (R)b, xc);
+  // source amplitude 2P/(pi r^2) and 1/r^2 formed once on the host
+  double r2 = ph.q_radius * ph.q_radius;
+  double qamp = ph.q_power != 0.0 ? 2.0 * ph.q_power / (M_PI * r2) : 0.0;
+  double ir2 = ph.q_power != 0.0 ? 1.0 / r2 : 0.0;
+  const int smem = (int)sizeof(ScalShared<R>);
+  cudaFuncSetAttribute(k_scalars<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_scalars<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
+      g, make_physr<R>(ph, g), tb, X, Sn, Y, dt, (R)a, (R)b, (R)xc, (R)ph.q_y0, (R)qamp, (R)ir2);
 }
 
 // ---------------------------------------------------------------------------
-// momentum predictor for component D on the low D-face of cell (i,j,k)
-template <int D, typename R>
-__device__ __forceinline__ R ldv(const Fields<R>& X, int comp, const Geo& g, int i, int j, int k) {
-  (void)D;
-  if (comp == 0) return ld_vel<0>(X.u[0], g, i, j, k);
-  if (comp == 1) return ld_vel<1>(X.u[1], g, i, j, k);
-  return ld_vel<2>(X.u[2], g, i, j, k);
+// momentum predictor
+
+// flux arrays for one component: [0] centre, [1] edge along t1, [2] edge along
+// t2; advective (a) and viscous (v) parts.  Extents kBZ+1 x kBY+1 x kBX+1
+// cover the one extra layer on any axis.
+template <typename R>
+struct MomFlux {
+  R a[3][kBZ + 1][kBY + 1][kBX + 1];
+  R v[3][kBZ + 1][kBY + 1][kBX + 1];
+};
+
+template <typename R>
+struct MomShared {
+  R u[3][Tile<3>::N];     // velocity components
+  R mu[Tile<1>::N];       // cell viscosity mu(alpha)
+  R a[Tile<1>::N];        // alpha
+  R T[Tile<1>::N];
+  R kap[Tile<1>::N];
+  R M[3][Tile<1>::N];
+  MomFlux<R> F;
+};
+
+template <int D>
+struct Tang {
+  static constexpr int t1 = D == 0 ? 1 : 0;
+  static constexpr int t2 = D == 2 ? 1 : 2;
+};
+
+template <int A>
+__device__ __forceinline__ void sh1(int& x, int& y, int& z, int s) {
+  if (A == 0) x += s;
+  if (A == 1) y += s;
+  if (A == 2) z += s;
 }
 
+// normal momentum fluxes of component D at the centre of local cell
+// (lx,ly,lz): advective U_c WENO5(u_D) with U_c the mean of the two D-faces,
+// viscous normal stress 2 mu du_D/dx_D
 template <int D, typename R>
-__device__ __forceinline__ R mu_at(const Fields<R>& X, const Geo& g, const Phys& ph, int i, int j,
-                                   int k) {
-  return mixp(ld_even(X.alpha, g, i, j, k), ph.mu);
+__device__ __forceinline__ void centre_flux(const MomShared<R>& S, const PhysR<R>& ph, int lx,
+                                            int ly, int lz, R& Fa, R& Fv) {
+  R v[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    int x = lx, y = ly, z = lz;
+    sh1<D>(x, y, z, m - 2);
+    v[m] = S.u[D][Tile<3>::at(x, y, z)];
+  }
+  const R Uc = R(0.5) * (v[2] + v[3]);
+  Fa = upwind_flux(Uc, v, ph.eps_u);
+  Fv = R(2) * S.mu[Tile<1>::at(lx, ly, lz)] * (v[3] - v[2]) * ph.ih;
 }
 
+// tangential fluxes of component D along T_ at the low T_-edge of the D-face
+// of local cell (lx,ly,lz): advective U_e WENO5(u_D along T_) with U_e the
+// mean of the two T_-faces at the edge, viscous mu_e (du_D/dx_T + du_T/dx_D)
+// with mu_e the mean of the four cells around the edge
 template <int D, int T_, typename R>
-__device__ __forceinline__ void tangential(const Fields<R>& X, const Geo& g, const Phys& ph, int i,
-                                           int j, int k, R ih, R& A, R& V) {
-  const R* ud = X.u[D];
-  const R* ut = X.u[T_];
-  R vals[7];
+__device__ __forceinline__ void edge_flux(const MomShared<R>& S, const PhysR<R>& ph, int lx,
+                                          int ly, int lz, R& Fa, R& Fv) {
+  R v[6];
 #pragma unroll
-  for (int m = 0; m < 7; ++m) {
-    int a = i, b = j, c = k;
-    shift<T_>(a, b, c, m - 3);
-    vals[m] = ld_vel<D>(ud, g, a, b, c);
+  for (int m = 0; m < 6; ++m) {
+    int x = lx, y = ly, z = lz;
+    sh1<T_>(x, y, z, m - 3);
+    v[m] = S.u[D][Tile<3>::at(x, y, z)];
   }
-  R Ge[2], te[2];
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    int a = i, b = j, c = k;           // f + s e_t
-    shift<T_>(a, b, c, s);
-    int a2 = a, b2 = b, c2 = c;        // f + s e_t - e_d
-    shift<D>(a2, b2, c2, -1);
-    R ut_hi = ld_vel<T_>(ut, g, a, b, c);
-    R ut_lo = ld_vel<T_>(ut, g, a2, b2, c2);
-    R Ue = R(0.5) * (ut_lo + ut_hi);
-    Ge[s] = upwind_flux(Ue, vals + s, (R)ph.eps_u);
-    int a3 = i, b3 = j, c3 = k;        // f + (s-1) e_t
-    shift<T_>(a3, b3, c3, s - 1);
-    int a4 = a3, b4 = b3, c4 = c3;     // f + (s-1) e_t - e_d
-    shift<D>(a4, b4, c4, -1);
-    R mue = R(0.25) * (mu_at<D>(X, g, ph, a, b, c) + mu_at<D>(X, g, ph, a2, b2, c2) +
-                       mu_at<D>(X, g, ph, a3, b3, c3) + mu_at<D>(X, g, ph, a4, b4, c4));
-    R dud_dt = (vals[3 + s] - vals[2 + s]) * ih;
-    R dut_dd = (ut_hi - ut_lo) * ih;
-    te[s] = mue * (dud_dt + dut_dd);
-  }
-  A -= (Ge[1] - Ge[0]) * ih;
-  V += (te[1] - te[0]) * ih;
+  int x2 = lx, y2 = ly, z2 = lz;   // f - e_D
+  sh1<D>(x2, y2, z2, -1);
+  const R ut_hi = S.u[T_][Tile<3>::at(lx, ly, lz)];
+  const R ut_lo = S.u[T_][Tile<3>::at(x2, y2, z2)];
+  const R Ue = R(0.5) * (ut_lo + ut_hi);
+  Fa = upwind_flux(Ue, v, ph.eps_u);
+  int x3 = lx, y3 = ly, z3 = lz;   // f - e_T
+  sh1<T_>(x3, y3, z3, -1);
+  int x4 = x3, y4 = y3, z4 = z3;   // f - e_T - e_D
+  sh1<D>(x4, y4, z4, -1);
+  const R mue = R(0.25) * (S.mu[Tile<1>::at(lx, ly, lz)] + S.mu[Tile<1>::at(x2, y2, z2)] +
+                           S.mu[Tile<1>::at(x3, y3, z3)] + S.mu[Tile<1>::at(x4, y4, z4)]);
+  const R dud_dt = (v[3] - v[2]) * ph.ih;
+  const R dut_dd = (ut_hi - ut_lo) * ph.ih;
+  Fv = mue * (dud_dt + dut_dd);
 }
 
 template <int D, typename R>
-__device__ __forceinline__ R momentum_face(const Fields<R>& X, const Geo& g, const Phys& ph,
-                                           const TBC& tb, const R* __restrict__ kappa,
-                                           const R* __restrict__ MD, int i, int j, int k, R dt) {
-  const R ih = R(1.0 / g.h);
-  const R* ud = X.u[D];
-  R nv[7];
-#pragma unroll
-  for (int m = 0; m < 7; ++m) {
-    int a = i, b = j, c = k;
-    shift<D>(a, b, c, m - 3);
-    nv[m] = ld_vel<D>(ud, g, a, b, c);
+__device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>& ph,
+                                                   MomShared<R>& S, const R* __restrict__ u_old,
+                                                   R* __restrict__ us, R dt) {
+  constexpr int t1 = Tang<D>::t1, t2 = Tang<D>::t2;
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int gi[3] = {i, j, k};
+  const bool inside = i < nx && j < ny && k < nz;
+  MomFlux<R>& F = S.F;
+  // centre fluxes: cell c at index t_D + 1; the low extra (c - e_D) at index 0
+  if (inside) {
+    int ci = tx, cj = ty, ck = tz;
+    sh1<D>(ci, cj, ck, 1);
+    centre_flux<D>(S, ph, tx, ty, tz, F.a[0][ck][cj][ci], F.v[0][ck][cj][ci]);
+    if (tsel<D>(tx, ty, tz) == 0) {
+      int x = tx, y = ty, z = tz;
+      sh1<D>(x, y, z, -1);
+      centre_flux<D>(S, ph, x, y, z, F.a[0][tz][ty][tx], F.v[0][tz][ty][tx]);
+    }
   }
-  // normal advection at the cell centres below (s=-1) and above (s=0) the face
-  R Fc[2], tau[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    int s = q - 1;
-    R Uc = R(0.5) * (nv[3 + s] + nv[4 + s]);
-    Fc[q] = upwind_flux(Uc, nv + 1 + s, (R)ph.eps_u);
-    int a = i, b = j, c = k;
-    shift<D>(a, b, c, s);
-    R muc = mu_at<D>(X, g, ph, a, b, c);
-    tau[q] = R(2) * muc * (nv[4 + s] - nv[3 + s]) * ih;
+  // edge fluxes along t1 and t2: low edge of face c at index t_T; the high
+  // extra at t_T + 1 (a thread one past the domain on T computes its own low
+  // edge, which is the high edge of the last cell)
+  if (inside || (gi[t1] == g.n[t1] && gi[D] < g.n[D] && gi[t2] < g.n[t2])) {
+    edge_flux<D, t1>(S, ph, tx, ty, tz, F.a[1][tz][ty][tx], F.v[1][tz][ty][tx]);
+    if (inside && tsel<t1>(tx, ty, tz) == tsel<t1>(kBX, kBY, kBZ) - 1) {
+      int x = tx, y = ty, z = tz;
+      sh1<t1>(x, y, z, 1);
+      edge_flux<D, t1>(S, ph, x, y, z, F.a[1][z][y][x], F.v[1][z][y][x]);
+    }
   }
-  R A = R(0) - (Fc[1] - Fc[0]) * ih;
-  R V = R(0) + (tau[1] - tau[0]) * ih;
-  if (D == 0) {
-    tangential<0, 1>(X, g, ph, i, j, k, ih, A, V);
-    tangential<0, 2>(X, g, ph, i, j, k, ih, A, V);
-  } else if (D == 1) {
-    tangential<1, 0>(X, g, ph, i, j, k, ih, A, V);
-    tangential<1, 2>(X, g, ph, i, j, k, ih, A, V);
-  } else {
-    tangential<2, 0>(X, g, ph, i, j, k, ih, A, V);
-    tangential<2, 1>(X, g, ph, i, j, k, ih, A, V);
+  if (inside || (gi[t2] == g.n[t2] && gi[D] < g.n[D] && gi[t1] < g.n[t1])) {
+    edge_flux<D, t2>(S, ph, tx, ty, tz, F.a[2][tz][ty][tx], F.v[2][tz][ty][tx]);
+    if (inside && tsel<t2>(tx, ty, tz) == tsel<t2>(kBX, kBY, kBZ) - 1) {
+      int x = tx, y = ty, z = tz;
+      sh1<t2>(x, y, z, 1);
+      edge_flux<D, t2>(S, ph, x, y, z, F.a[2][z][y][x], F.v[2][z][y][x]);
+    }
   }
-  // forces on the face between cell L = c - e_D and R = c
-  int a = i, b = j, c = k;
-  shift<D>(a, b, c, -1);
-  R alL = ld_even(X.alpha, g, a, b, c), alR = ld_even(X.alpha, g, i, j, k);
-  R rho_f = R(0.5) * (mixp(alL, ph.rho) + mixp(alR, ph.rho));
-  R sig_f = R(0.5) * (sigma_of_T(ld_T(X.T, g, tb, a, b, c), ph) + sigma_of_T(ld_T(X.T, g, tb, i, j, k), ph));
-  R kap_f = R(0.5) * (ld_even(kappa, g, a, b, c) + ld_even(kappa, g, i, j, k));
-  R jump = (alR - alL) * ih;
-  R fn = -sig_f * kap_f * jump;
-  R fM = R(0.5) * (ld_even(MD, g, a, b, c) + ld_even(MD, g, i, j, k));
-  return nv[3] + dt * (A + (V + fn + fM) / rho_f + (R)ph.g[D]);
+  __syncthreads();
+  if (inside) {
+    const int c = (k * ny + j) * nx + i;
+    if (g.bc[D] == WALL && gi[D] == 0) {
+      us[c] = R(0);
+    } else {
+      const R ih = ph.ih;
+      int ci = tx, cj = ty, ck = tz;
+      sh1<D>(ci, cj, ck, 1);
+      R A = R(0) - (F.a[0][ck][cj][ci] - F.a[0][tz][ty][tx]) * ih;
+      R V = R(0) + (F.v[0][ck][cj][ci] - F.v[0][tz][ty][tx]) * ih;
+      {
+        int x = tx, y = ty, z = tz;
+        sh1<t1>(x, y, z, 1);
+        A -= (F.a[1][z][y][x] - F.a[1][tz][ty][tx]) * ih;
+        V += (F.v[1][z][y][x] - F.v[1][tz][ty][tx]) * ih;
+      }
+      {
+        int x = tx, y = ty, z = tz;
+        sh1<t2>(x, y, z, 1);
+        A -= (F.a[2][z][y][x] - F.a[2][tz][ty][tx]) * ih;
+        V += (F.v[2][z][y][x] - F.v[2][tz][ty][tx]) * ih;
+      }
+      // forces on the face between cell L = c - e_D and R = c
+      int x = tx, y = ty, z = tz;
+      sh1<D>(x, y, z, -1);
+      const int cl = Tile<1>::at(x, y, z), cr = Tile<1>::at(tx, ty, tz);
+      const R alL = S.a[cl], alR = S.a[cr];
+      const R rho_f = R(0.5) * (mixr(alL, ph.rho) + mixr(alR, ph.rho));
+      const R sig_f = R(0.5) * (sigma_r(S.T[cl], ph) + sigma_r(S.T[cr], ph));
+      const R kap_f = R(0.5) * (S.kap[cl] + S.kap[cr]);
+      const R jump = (alR - alL) * ih;
+      const R fn = -sig_f * kap_f * jump;
+      const R fM = R(0.5) * (S.M[D][cl] + S.M[D][cr]);
+      us[c] = S.u[D][Tile<3>::at(tx, ty, tz)] + dt * (A + (V + fn + fM) / rho_f + ph.g[D]);
+    }
+  }
+  __syncthreads();
 }
 
 template <typename R>
-__global__ void k_momentum(Geo g, Phys ph, TBC tb, Fields<R> X, const R* __restrict__ kappa,
-                           const R* __restrict__ M0, const R* __restrict__ M1,
-                           const R* __restrict__ M2, R* __restrict__ us0, R* __restrict__ us1,
-                           R* __restrict__ us2, const double* __restrict__ dtp) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
-  int i, j, k;
-  decode(g, c, i, j, k);
-  const R dt = (R)(*dtp);
-  us0[c] = (g.bc[0] == WALL && i == 0) ? R(0) : momentum_face<0>(X, g, ph, tb, kappa, M0, i, j, k, dt);
-  us1[c] = (g.bc[1] == WALL && j == 0) ? R(0) : momentum_face<1>(X, g, ph, tb, kappa, M1, i, j, k, dt);
-  us2[c] = (g.bc[2] == WALL && k == 0) ? R(0) : momentum_face<2>(X, g, ph, tb, kappa, M2, i, j, k, dt);
+__global__ void __launch_bounds__(kThreads)
+    k_momentum(Geo g, PhysR<R> ph, TBC tb, Fields<R> X, const R* __restrict__ kappa,
+               const R* __restrict__ M0, const R* __restrict__ M1, const R* __restrict__ M2,
+               R* __restrict__ us0, R* __restrict__ us1, R* __restrict__ us2,
+               const double* __restrict__ dtp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MomShared<R>& S = *reinterpret_cast<MomShared<R>*>(smem_raw);
+  stage<3, F_VEL, 0>(S.u[0], X.u[0], g, tb);
+  stage<3, F_VEL, 1>(S.u[1], X.u[1], g, tb);
+  stage<3, F_VEL, 2>(S.u[2], X.u[2], g, tb);
+  stage<1, F_EVEN, 0>(S.a, X.alpha, g, tb);
+  stage<1, F_TEMP, 0>(S.T, X.T, g, tb);
+  stage<1, F_EVEN, 0>(S.kap, kappa, g, tb);
+  stage<1, F_EVEN, 0>(S.M[0], M0, g, tb);
+  stage<1, F_EVEN, 0>(S.M[1], M1, g, tb);
+  stage<1, F_EVEN, 0>(S.M[2], M2, g, tb);
+  __syncthreads();
+  for (int e = flat_tid(); e < Tile<1>::N; e += kThreads) S.mu[e] = mixr(S.a[e], ph.mu);
+  __syncthreads();
+  const R dt = (R)dtp[0];
+  momentum_component<0>(g, ph, S, X.u[0], us0, dt);
+  momentum_component<1>(g, ph, S, X.u[1], us1, dt);
+  momentum_component<2>(g, ph, S, X.u[2], us2, dt);
 }
 
 template <typename R>
 void launch_momentum(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, const R* kappa,
                      const R* M0, const R* M1, const R* M2, R* us0, R* us1, R* us2,
                      const double* dt, cudaStream_t s) {
-  k_momentum<R><<<grid1d(g.N, 128), 128, 0, s>>>(g, ph, tb, X, kappa, M0, M1, M2, us0, us1, us2, dt);
+  const int smem = (int)sizeof(MomShared<R>);
+  cudaFuncSetAttribute(k_momentum<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_momentum<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
+      g, make_physr<R>(ph, g), tb, X, kappa, M0, M1, M2, us0, us1, us2, dt);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,18 +690,18 @@ template <typename R>
 __global__ void k_div_rhs(Geo g, const R* __restrict__ u0, const R* __restrict__ u1,
                           const R* __restrict__ u2, const double* __restrict__ dtp,
                           double* __restrict__ b, double* __restrict__ partial) {
-  const double ih = 1.0 / g.h;
-  const double dt = *dtp;
+  const double ih = g.ih;
+  const double idt = dtp[1];
   double acc = 0.0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.N;
        c += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     decode(g, c, i, j, k);
     double dv = 0.0;
-    dv += ((double)ld_vel<0>(u0, g, i + 1, j, k) - (double)ld_vel<0>(u0, g, i, j, k)) * ih;
-    dv += ((double)ld_vel<1>(u1, g, i, j + 1, k) - (double)ld_vel<1>(u1, g, i, j, k)) * ih;
-    dv += ((double)ld_vel<2>(u2, g, i, j, k + 1) - (double)ld_vel<2>(u2, g, i, j, k)) * ih;
-    double v = -dv / dt;
+    dv += ((double)ld_vel<0>(u0, g, i + 1, j, k) - (double)u0[c]) * ih;
+    dv += ((double)ld_vel<1>(u1, g, i, j + 1, k) - (double)u1[c]) * ih;
+    dv += ((double)ld_vel<2>(u2, g, i, j, k + 1) - (double)u2[c]) * ih;
+    double v = -dv * idt;
     b[c] = v;
     acc += v;
   }
@@ -431,19 +740,19 @@ void launch_beta(const Geo& g, const Phys& ph, const R* alpha, B* b0, B* b1, B* 
 }
 
 // ---------------------------------------------------------------------------
-// velocity correction and RK combination
+// velocity correction and RK combination.  The pressure difference is taken
+// in double; in the mixed form the rest is float arithmetic.
 template <typename R, typename B>
 __global__ void k_correct(Geo g, Fields<R> Sn, Fields<R> Y, const R* __restrict__ us0,
                           const R* __restrict__ us1, const R* __restrict__ us2,
                           const double* __restrict__ p, const B* __restrict__ b0,
                           const B* __restrict__ b1, const B* __restrict__ b2,
-                          const double* __restrict__ dtp, double a, double bb) {
+                          const double* __restrict__ dtp, R a, R bb) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= g.N) return;
   int i, j, k;
   decode(g, c, i, j, k);
-  const double dt = *dtp;
-  const double ih = 1.0 / g.h;
+  const double dtih = dtp[0] * g.ih;
   const double pc = p[c];
   const R* us[3] = {us0, us1, us2};
   const B* be[3] = {b0, b1, b2};
@@ -453,11 +762,11 @@ __global__ void k_correct(Geo g, Fields<R> Sn, Fields<R> Y, const R* __restrict_
     bool wall_face = (g.bc[d] == WALL && idx[d] == 0);
     int m[3] = {i, j, k};
     m[d] = wrapi(m[d] - 1, g.n[d]);
-    double pl = p[lin(g, m[0], m[1], m[2])];
-    double ucorr = (double)us[d][c] - dt * (double)be[d][c] * (pc - pl) * ih;
-    double un = (double)Sn.u[d][c];
-    double out = wall_face ? 0.0 : a * un + bb * ucorr;
-    Y.u[d][c] = (R)out;
+    double pl = p[(m[2] * g.n[1] + m[1]) * g.n[0] + m[0]];
+    R gp = (R)((pc - pl) * dtih);
+    R ucorr = us[d][c] - (R)be[d][c] * gp;
+    R out = wall_face ? R(0) : a * Sn.u[d][c] + bb * ucorr;
+    Y.u[d][c] = out;
   }
 }
 
@@ -465,7 +774,7 @@ template <typename R, typename B>
 void launch_correct(const Geo& g, Fields<R> Sn, Fields<R> Y, R* const* us, const double* p,
                     B* const* beta, const double* dt, double a, double b, cudaStream_t s) {
   k_correct<R, B><<<grid1d(g.N, 256), 256, 0, s>>>(g, Sn, Y, us[0], us[1], us[2], p, beta[0],
-                                                   beta[1], beta[2], dt, a, b);
+                                                   beta[1], beta[2], dt, (R)a, (R)b);
 }
 
 // ---------------------------------------------------------------------------
@@ -510,6 +819,7 @@ void launch_dt_reduce(const Geo& g, const Phys& ph, Fields<R> X, unsigned long l
   k_dt_reduce<R><<<kRedBlocks, 256, 0, s>>>(g, ph, X, maxbits, nanflag);
 }
 
+// dt[0] = step, dt[1] = 1/step
 __global__ void k_dt_final(double h, double rho_sum, double cfl, double c_cap, double c_visc,
                            double c_therm, double dt_max, const unsigned long long* maxbits,
                            double* dt, int* limiter) {
@@ -526,7 +836,8 @@ __global__ void k_dt_final(double h, double rho_sum, double cfl, double c_cap, d
   int kk = 0;
   for (int q = 1; q < 5; ++q)
     if (lim[q] < lim[kk]) kk = q;
-  *dt = lim[kk];
+  dt[0] = lim[kk];
+  dt[1] = 1.0 / lim[kk];
   *limiter = kk;
 }
 
@@ -537,9 +848,14 @@ void launch_dt_final(const Geo& g, const Phys& ph, double cfl, double c_cap, dou
                              maxbits, dt, limiter);
 }
 
-__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
+__global__ void k_set_scalar(double* dst, double v, double iv) {
+  dst[0] = v;
+  dst[1] = iv;
+}
 
-void launch_set_scalar(double* dst, double v, cudaStream_t s) { k_set_scalar<<<1, 1, 0, s>>>(dst, v); }
+void launch_set_scalar(double* dst, double v, cudaStream_t s) {
+  k_set_scalar<<<1, 1, 0, s>>>(dst, v, 1.0 / v);
+}
 
 // ---------------------------------------------------------------------------
 // diagnostics: partial sums of alpha and rho(alpha) (two slots per block),
@@ -548,7 +864,7 @@ template <typename R>
 __global__ void k_diagnostics(Geo g, Phys ph, Fields<R> X, const double* __restrict__ p,
                               double* __restrict__ partial, unsigned long long* __restrict__ maxbits,
                               int* __restrict__ nanflag) {
-  const double ih = 1.0 / g.h;
+  const double ih = g.ih;
   double sa = 0.0, sm = 0.0;
   unsigned long long mdiv = 0;
   int bad = 0;
@@ -595,7 +911,7 @@ void launch_diagnostics(const Geo& g, const Phys& ph, Fields<R> X, const double*
 // ---------------------------------------------------------------------------
 #define FVM_INST(R)                                                                              \
   template void launch_smooth<R>(const Geo&, const R*, R*, cudaStream_t);                        \
-  template void launch_interface<R>(const Geo&, const Phys&, const TBC&, const R*, const R*,     \
+  template void launch_interface<R>(const Geo&, const Phys&, const TBC&, int, const R*,          \
                                     const R*, R*, R*, R*, R*, cudaStream_t);                     \
   template void launch_scalars<R>(const Geo&, const Phys&, const TBC&, Fields<R>, Fields<R>,     \
                                   Fields<R>, const double*, double, double, double,              \
