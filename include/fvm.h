@@ -138,6 +138,31 @@ fvm_status fvm_step(fvm_ctx* ctx, fvm_state* st, long step_index, double dt,
 fvm_status fvm_poisson_solve(fvm_ctx* ctx, const void* alpha, const double* rhs,
                              double* p, fvm_step_info* info);
 
+/* Allocation-free variant of fvm_poisson_solve (the paper has no
+ * counterpart: this serves callers that cannot allocate device memory, such
+ * as a plugin inside a host application that owns the whole device memory
+ * pool, or a real-time loop that must not allocate once running).
+ * No context and no workspace: the solve's scratch lives in a static device
+ * array of 16 MiB inside the library (held by every GPU that loads it until
+ * exit), so nothing is allocated by the caller or by this call.
+ *   prm      parameters as for fvm_create(); only the grid, boundary kinds,
+ *            rho, the multigrid fields and precision are used.  Grids whose
+ *            solve needs more than the 16 MiB (64^3 cells fit in both
+ *            precisions) return FVM_ENOMEM before any device work.
+ *   alpha    device, nx*ny*nz double (FVM_F64) or float (FVM_MIXED)
+ *   rhs      device, nx*ny*nz double; read only (made mean-free on a copy)
+ *   p        device, nx*ny*nz double: initial guess in, mean-free solution out
+ *   cuda_stream  cudaStream_t for all work (NULL = legacy default stream)
+ *   info     may be NULL; vcycles[0] and rel_residual[0] report the solve
+ * Same arithmetic and status codes as fvm_poisson_solve (no fvm_last_error
+ * message: there is no context).  The first call on a device looks up the
+ * array's device address with cudaGetSymbolAddress, so make it before any
+ * stream capture on that device.  Every call shares the array; calls that
+ * overlap on the GPU (several streams or host threads at once) race. */
+fvm_status fvm_poisson_solve_noalloc(const fvm_params* prm, const void* alpha,
+                                     const double* rhs, double* p, void* cuda_stream,
+                                     fvm_step_info* info);
+
 /* Reverse-mode (adjoint) of one step: not implemented in this library yet;
  * returns FVM_EUNSUPPORTED. */
 fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index,

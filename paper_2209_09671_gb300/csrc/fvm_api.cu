@@ -770,3 +770,166 @@ const char* fvm_last_error(const fvm_ctx* ctx) { return ctx ? ctx->err : "no con
 const char* fvm_version(void) { return "fvm-gb300 0.1"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free pressure solve.
+//
+// Some callers cannot call cudaMalloc: a plugin running inside a host
+// application that owns the whole device memory pool and hands the library
+// only its own field pointers, or real-time loops where any allocation is
+// forbidden once running.  fvm_poisson_solve_noalloc() serves them: it keeps
+// its scratch in the file-scope device array below, so neither it nor the
+// caller allocates anything.  The array is sized for grids of up to 64^3
+// cells and is held by every GPU that loads the library, until exit.
+//
+// In host code the array's name is only a host-side stand-in, never a device
+// address.  The first call on each device therefore looks up the real
+// address with cudaGetSymbolAddress() while that device is current and keeps
+// it for the device; make that first call before any stream capture.  All
+// calls share the one array and it keeps the previous call's contents: the
+// solve initialises every scratch value it reads (the right-hand side copy,
+// the face coefficients, each level's correction, the reduction slots), and
+// calls that overlap on the GPU (other streams, other host threads) race on
+// the array.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+void* g_noalloc_ptr[kNoAllocMaxDevices];
+
+// device address of the scratch array on the current device (set up once)
+fvm_status noalloc_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return FVM_ECUDA;
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return FVM_ECUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FVM_OK;
+}
+
+// layout of the pressure solve's scratch only (no stage buffers)
+size_t plan_noalloc(const fvm_params& p, fvm_ctx* c, char* base) {
+  Plan pl;
+  LevelShape lv[kMaxLevels];
+  const int nl = build_levels(p, lv);
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  const bool mixed = p.precision == FVM_MIXED;
+  const size_t ms = mixed ? sizeof(float) : sizeof(double);
+  size_t o_b = pl.take(N * sizeof(double));
+  size_t o_beta[3];
+  for (int q = 0; q < 3; ++q) o_beta[q] = pl.take(N * ms);
+  size_t o_e = 0, o_r = 0;
+  if (mixed) {
+    o_e = pl.take(N * sizeof(float));
+    o_r = pl.take(N * sizeof(float));
+  }
+  size_t o_lx[kMaxLevels], o_lb[kMaxLevels], o_lbeta[kMaxLevels][3];
+  for (int l = 1; l < nl; ++l) {
+    const long long n = (long long)lv[l].n[0] * lv[l].n[1] * lv[l].n[2];
+    o_lx[l] = pl.take(n * ms);
+    o_lb[l] = pl.take(n * ms);
+    for (int q = 0; q < 3; ++q) o_lbeta[l][q] = pl.take(n * ms);
+  }
+  const long long nc = (long long)lv[nl - 1].n[0] * lv[nl - 1].n[1] * lv[nl - 1].n[2];
+  size_t o_cg[3];
+  for (int q = 0; q < 3; ++q) o_cg[q] = pl.take((q == 2 ? 2 : 1) * nc * sizeof(double));
+  size_t o_part = pl.take(2 * kRedBlocks * sizeof(double));
+  size_t o_scal = pl.take(16 * sizeof(double));
+  if (c) {
+    c->b = (double*)(base + o_b);
+    for (int q = 0; q < 3; ++q) c->beta0[q] = base + o_beta[q];
+    c->e32 = mixed ? (float*)(base + o_e) : nullptr;
+    c->r32 = mixed ? (float*)(base + o_r) : nullptr;
+    c->nlev = nl;
+    for (int l = 0; l < nl; ++l) c->shp[l] = lv[l];
+    for (int l = 1; l < nl; ++l) {
+      c->lx[l] = base + o_lx[l];
+      c->lb[l] = base + o_lb[l];
+      for (int q = 0; q < 3; ++q) c->lbeta[l][q] = base + o_lbeta[l][q];
+    }
+    for (int q = 0; q < 3; ++q) c->cg[q] = base + o_cg[q];
+    c->partial = (double*)(base + o_part);
+    c->scal = (double*)(base + o_scal);
+  }
+  return pl.off;
+}
+
+// material constants of the solve, as fvm_create() sets them
+void noalloc_physics(const fvm_params* prm, fvm_ctx* c) {
+  for (int q = 0; q < 2; ++q) {
+    c->ph.rho[q] = prm->rho[q];
+    c->ph.mu[q] = prm->mu[q];
+    c->ph.lam[q] = prm->lambda[q];
+    c->ph.rcp[q] = prm->rho[q] * prm->cp[q];
+  }
+  c->ph.eps_n = 1e-8 / prm->h;
+  c->ph.L[0] = prm->nx * prm->h;
+  c->ph.L[1] = prm->ny * prm->h;
+  c->ph.L[2] = prm->nz * prm->h;
+  c->tb.axis = -1;
+}
+
+}  // namespace
+
+extern "C" fvm_status fvm_poisson_solve_noalloc(const fvm_params* prm, const void* alpha,
+                                                const double* rhs, double* p, void* cuda_stream,
+                                                fvm_step_info* info) {
+  if (check_params(prm) || !alpha || !rhs || !p) return FVM_EINVAL;
+  if (plan_noalloc(*prm, nullptr, nullptr) > kNoAllocScratchBytes) return FVM_ENOMEM;
+  void* base = nullptr;
+  fvm_status st = noalloc_scratch(&base);
+  if (st) return st;
+  cudaGetLastError();
+  fvm_ctx c;                       // host stack only: nothing is allocated
+  memset(&c, 0, sizeof(c));
+  c.prm = *prm;
+  c.stream = (cudaStream_t)cuda_stream;
+  c.mixed = prm->precision == FVM_MIXED;
+  c.rsz = c.mixed ? sizeof(float) : sizeof(double);
+  c.ws = (char*)base;
+  c.ws_bytes = kNoAllocScratchBytes;
+  plan_noalloc(*prm, &c, (char*)base);
+  c.g = make_geo(*prm, c.shp[0]);
+  noalloc_physics(prm, &c);
+  cudaStream_t s = c.stream;
+  const Geo& g = c.g;
+  cudaError_t e = cudaMemcpyAsync(c.b, rhs, g.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FVM_ECUDA;
+  }
+  TIMED(&c, FVM_K_MISC, 2, launch_sum_field<double>(c.b, g.N, false, c.partial, c.scal + 3, s));
+  TIMED(&c, FVM_K_MISC, 1, launch_sub_mean(c.b, g.N, c.scal + 3, s));
+  int cyc = 0;
+  double rel = 0.0;
+  if (c.mixed) {
+    float* be[3] = {(float*)c.beta0[0], (float*)c.beta0[1], (float*)c.beta0[2]};
+    TIMED(&c, FVM_K_BETA, 1, launch_beta<float, float>(g, c.ph, (const float*)alpha, be[0], be[1], be[2], s));
+    st = solve_mixed(&c, p, c.b, &cyc, &rel, info != nullptr);
+  } else {
+    double* be[3] = {(double*)c.beta0[0], (double*)c.beta0[1], (double*)c.beta0[2]};
+    TIMED(&c, FVM_K_BETA, 1, launch_beta<double, double>(g, c.ph, (const double*)alpha, be[0], be[1], be[2], s));
+    st = solve_f64(&c, p, c.b, &cyc, &rel, info != nullptr);
+  }
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->vcycles[0] = cyc;
+    info->rel_residual[0] = rel;
+    info->dt_limiter = -1;
+  }
+  if (st) return st;
+  return cuda_check(&c, "poisson (no allocation)");
+}

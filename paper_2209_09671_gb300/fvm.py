@@ -64,7 +64,7 @@ class fvm_step_info(ctypes.Structure):
 
 EXPORTS = ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step", "fvm_poisson_solve",
            "fvm_step_adjoint", "fvm_status_string", "fvm_last_error", "fvm_version",
-           "fvm_profile", "fvm_profile_read", "fvm_launch_count")
+           "fvm_profile", "fvm_profile_read", "fvm_launch_count", "fvm_poisson_solve_noalloc")
 
 KERNEL_CLASSES = ("smooth", "interface", "scalars", "momentum", "div_rhs", "beta", "gs_fine",
                   "gs_coarse", "restrict_fine", "restrict_coarse", "prolong_fine",
@@ -102,10 +102,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fvm_version.restype = ctypes.c_char_p
     lib.fvm_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.fvm_launch_count.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_long)]
+    lib.fvm_poisson_solve_noalloc.argtypes = [P(fvm_params), ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, P(fvm_step_info)]
     lib.fvm_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_long),
                                      P(ctypes.c_double)]
     for name in ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step",
-                 "fvm_poisson_solve", "fvm_step_adjoint", "fvm_profile", "fvm_profile_read", "fvm_launch_count"):
+                 "fvm_poisson_solve", "fvm_step_adjoint", "fvm_profile", "fvm_profile_read", "fvm_launch_count",
+                 "fvm_poisson_solve_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -261,6 +264,25 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def fvm_poisson_solve_noalloc(params, alpha, rhs, p, stream=None) -> dict:
+    """The allocation-free pressure solve (no context, no workspace): for
+    callers that cannot allocate device memory.  alpha, rhs, p are CUDA
+    tensors as for Solver.fvm_poisson_solve; the stream defaults to torch's
+    current stream.  Returns the info dict with the status."""
+    import torch
+    lib = load()
+    cp = params if isinstance(params, fvm_params) else make_params(params)
+    if stream is None:
+        stream = torch.cuda.current_stream(p.device)
+    inf = fvm_step_info()
+    rc = lib.fvm_poisson_solve_noalloc(ctypes.byref(cp), ctypes.c_void_p(alpha.data_ptr()),
+                                       ctypes.c_void_p(rhs.data_ptr()), ctypes.c_void_p(p.data_ptr()),
+                                       ctypes.c_void_p(stream.cuda_stream), ctypes.byref(inf))
+    out = inf.as_dict()
+    out["status"] = rc
+    return out
 
 
 def to_device(state: dict, mixed: bool, device="cuda") -> dict:
