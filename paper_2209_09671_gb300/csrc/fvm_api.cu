@@ -152,6 +152,10 @@ struct fvm_ctx {
   cudaEvent_t* prof_ev;      // 2 * kProfSlots events
   int* prof_cls;
   long nlaunch;              // kernels launched since the last count reset
+  // CUDA graphs of the mixed-form refinement iteration, keyed by (p, alpha)
+  int graphs_ok;             // 1: try stream capture; 0: eager launches only
+  struct GEntry { const void* p; const void* a; cudaGraphExec_t exec; long nk; } gcache[6];
+  int gnext;
   long prof_launches[FVM_KCLASS_COUNT];
   double prof_ms[FVM_KCLASS_COUNT];
   char err[512];
@@ -322,6 +326,19 @@ void coarsen_betas(fvm_ctx* c, MGLevel<T>* Ls) {
     TIMED(c, FVM_K_BETA, 1, launch_beta_coarsen<T>(Ls[l], Ls[l + 1], c->stream));
 }
 
+// `iters` Gauss-Seidel iterations on level l: a sweep of colour `first`,
+// then one of the other colour
+template <typename T>
+void smooth(fvm_ctx* c, MGLevel<T>& L, int l, int iters, int first) {
+  const int kg = l == 0 ? FVM_K_GS_FINE : FVM_K_GS_COARSE;
+  for (int q = 0; q < iters; ++q) {
+    for (int col = 0; col < 2; ++col)
+      TIMED(c, kg, 1, launch_gs<T>(L, col == 0 ? first : 1 - first, c->stream));
+  }
+}
+
+// V(pre, post) cycle: red-black sweeps before the coarse correction,
+// black-red after, CG on the coarsest level
 template <typename T>
 void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
   cudaStream_t s = c->stream;
@@ -330,20 +347,13 @@ void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
                                                    coarse_rtol, c->prm.coarse_maxit, s));
     return;
   }
-  const int kg = l == 0 ? FVM_K_GS_FINE : FVM_K_GS_COARSE;
-  for (int q = 0; q < c->prm.mg_pre; ++q) {
-    TIMED(c, kg, 1, launch_gs<T>(Ls[l], 0, s));
-    TIMED(c, kg, 1, launch_gs<T>(Ls[l], 1, s));
-  }
+  smooth<T>(c, Ls[l], l, c->prm.mg_pre, 0);
   TIMED(c, l == 0 ? FVM_K_RESTRICT_FINE : FVM_K_RESTRICT_COARSE, 1,
         launch_residual_restrict<T>(Ls[l], Ls[l + 1], s));
   vcycle<T>(c, Ls, l + 1, coarse_rtol);
   TIMED(c, l == 0 ? FVM_K_PROLONG_FINE : FVM_K_PROLONG_COARSE, 1,
         launch_prolong<T>(Ls[l], Ls[l + 1], s));
-  for (int q = 0; q < c->prm.mg_post; ++q) {
-    TIMED(c, kg, 1, launch_gs<T>(Ls[l], 1, s));
-    TIMED(c, kg, 1, launch_gs<T>(Ls[l], 0, s));
-  }
+  smooth<T>(c, Ls[l], l, c->prm.mg_post, 1);
 }
 
 // F64: L p = b (b mean-free, double), beta0 already computed
@@ -404,9 +414,61 @@ fvm_status solve_f64(fvm_ctx* c, double* p, double* b, int* cycles_out, double* 
   return FVM_OK;
 }
 
-// MIXED: double defect correction around float V-cycles
-fvm_status solve_mixed(fvm_ctx* c, double* p, double* b, int* cycles_out, double* rel_out,
-                       bool want_rel) {
+// MIXED: double defect correction around float V-cycles.  One refinement
+// iteration is: e = 0; mx_inner_cycles float V-cycles on L e = r; p += e;
+// r = b - L p in double (stored as float for the next iteration) and its
+// norm.  It has no host synchronisation, so after the first use it is
+// replayed as a CUDA graph (keyed by the p and alpha pointers) unless
+// profiling is on or the stream cannot be captured.
+void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, double* b,
+                 float* const* be, double crtol) {
+  cudaStream_t s = c->stream;
+  const long long N = c->g.N;
+  TIMED(c, FVM_K_MISC, 1, launch_zero<float>(c->e32, N, s));
+  for (int q = 0; q < c->prm.mx_inner_cycles; ++q) vcycle<float>(c, Ls, 0, crtol);
+  TIMED(c, FVM_K_ADD_CORRECTION, 1, launch_add_correction(N, p, c->e32, s));
+  TIMED(c, FVM_K_RESIDUAL64, 2, launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, s));
+}
+
+cudaGraphExec_t refine_graph(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p,
+                             double* b, float* const* be, double crtol, long* nk) {
+  for (int q = 0; q < 6; ++q)
+    if (c->gcache[q].exec && c->gcache[q].p == p && c->gcache[q].a == alpha) {
+      *nk = c->gcache[q].nk;
+      return c->gcache[q].exec;
+    }
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->graphs_ok = 0;
+    return nullptr;
+  }
+  const long n0 = c->nlaunch;
+  refine_once(c, Ls, alpha, p, b, be, crtol);
+  const long captured = c->nlaunch - n0;
+  c->nlaunch = n0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess || !graph ||
+      cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    c->graphs_ok = 0;
+    return nullptr;
+  }
+  cudaGraphDestroy(graph);
+  auto& slot = c->gcache[c->gnext];
+  if (slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot.p = p;
+  slot.a = alpha;
+  slot.exec = exec;
+  slot.nk = captured;
+  c->gnext = (c->gnext + 1) % 6;
+  *nk = captured;
+  return exec;
+}
+
+fvm_status solve_mixed(fvm_ctx* c, const float* alpha, double* p, double* b, int* cycles_out,
+                       double* rel_out, bool want_rel) {
   (void)want_rel;
   cudaStream_t s = c->stream;
   MGLevel<float> Ls[kMaxLevels];
@@ -430,8 +492,8 @@ fvm_status solve_mixed(fvm_ctx* c, double* p, double* b, int* cycles_out, double
   const double crtol = c->prm.coarse_rtol > 1e-6 ? c->prm.coarse_rtol : 1e-6;
   int outer = 0;
   double rel = 0.0;
+  TIMED(c, FVM_K_RESIDUAL64, 2, launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, s));
   for (;;) {
-    TIMED(c, FVM_K_RESIDUAL64, 2, launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, s));
     if (fixed > 0) {
       if (outer == fixed) {
         double r2;
@@ -448,9 +510,15 @@ fvm_status solve_mixed(fvm_ctx* c, double* p, double* b, int* cycles_out, double
       if (!isfinite(rel)) return set_err(c, FVM_EUNSTABLE, "non-finite pressure residual");
       if (rel <= c->prm.mg_rtol || outer >= c->prm.mg_max_cycles) break;
     }
-    TIMED(c, FVM_K_MISC, 1, launch_zero<float>(c->e32, N, s));
-    for (int q = 0; q < c->prm.mx_inner_cycles; ++q) vcycle<float>(c, Ls, 0, crtol);
-    TIMED(c, FVM_K_ADD_CORRECTION, 1, launch_add_correction(N, p, c->e32, s));
+    cudaGraphExec_t exec = nullptr;
+    long nk = 0;
+    if (c->graphs_ok && !c->prof) exec = refine_graph(c, Ls, alpha, p, b, be, crtol, &nk);
+    if (exec) {
+      if (cudaGraphLaunch(exec, s) != cudaSuccess) return cuda_check(c, "graph launch");
+      c->nlaunch += nk;
+    } else {
+      refine_once(c, Ls, alpha, p, b, be, crtol);
+    }
     ++outer;
   }
   TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(p, N, false, c->partial, c->scal + 2, s));
@@ -496,7 +564,7 @@ fvm_status stage(fvm_ctx* c, Fields<R> X, Fields<R> Sn, Fields<R> Y, double* p, 
   if (c->mixed) {
     float* be[3] = {(float*)c->beta0[0], (float*)c->beta0[1], (float*)c->beta0[2]};
     TIMED(c, FVM_K_BETA, 1, launch_beta<R, float>(g, c->ph, (const R*)X.alpha, be[0], be[1], be[2], s));
-    st = solve_mixed(c, p, c->b, cyc, rel, want_rel);
+    st = solve_mixed(c, (const float*)X.alpha, p, c->b, cyc, rel, want_rel);
     if (st && st != FVM_ENOCONV) return st;
     TIMED(c, FVM_K_CORRECT, 1, launch_correct<R, float>(g, Sn, Y, us, p, be, c->dt_dev, ca, cb, s));
   } else {
@@ -647,6 +715,7 @@ fvm_status fvm_create(const fvm_params* prm, void* workspace, size_t bytes, void
       tb.Ls = ph.L[tb.s_axis];
     }
   }
+  c->graphs_ok = 1;
   snprintf(c->err, sizeof(c->err), "ok");
   *out = c;
   return FVM_OK;
@@ -654,6 +723,8 @@ fvm_status fvm_create(const fvm_params* prm, void* workspace, size_t bytes, void
 
 fvm_status fvm_destroy(fvm_ctx* ctx) {
   if (!ctx) return FVM_EINVAL;
+  for (int q = 0; q < 6; ++q)
+    if (ctx->gcache[q].exec) cudaGraphExecDestroy(ctx->gcache[q].exec);
   if (ctx->prof_ev) {
     for (int q = 0; q < 2 * kProfSlots; ++q) cudaEventDestroy(ctx->prof_ev[q]);
     free(ctx->prof_ev);
@@ -728,7 +799,7 @@ fvm_status fvm_poisson_solve(fvm_ctx* ctx, const void* alpha, const double* rhs,
   if (ctx->mixed) {
     float* be[3] = {(float*)ctx->beta0[0], (float*)ctx->beta0[1], (float*)ctx->beta0[2]};
     TIMED(ctx, FVM_K_BETA, 1, launch_beta<float, float>(g, ctx->ph, (const float*)alpha, be[0], be[1], be[2], s));
-    st = solve_mixed(ctx, p, ctx->b, &cyc, &rel, info != nullptr);
+    st = solve_mixed(ctx, (const float*)alpha, p, ctx->b, &cyc, &rel, info != nullptr);
   } else {
     double* be[3] = {(double*)ctx->beta0[0], (double*)ctx->beta0[1], (double*)ctx->beta0[2]};
     TIMED(ctx, FVM_K_BETA, 1, launch_beta<double, double>(g, ctx->ph, (const double*)alpha, be[0], be[1], be[2], s));
@@ -918,7 +989,7 @@ extern "C" fvm_status fvm_poisson_solve_noalloc(const fvm_params* prm, const voi
   if (c.mixed) {
     float* be[3] = {(float*)c.beta0[0], (float*)c.beta0[1], (float*)c.beta0[2]};
     TIMED(&c, FVM_K_BETA, 1, launch_beta<float, float>(g, c.ph, (const float*)alpha, be[0], be[1], be[2], s));
-    st = solve_mixed(&c, p, c.b, &cyc, &rel, info != nullptr);
+    st = solve_mixed(&c, (const float*)alpha, p, c.b, &cyc, &rel, info != nullptr);
   } else {
     double* be[3] = {(double*)c.beta0[0], (double*)c.beta0[1], (double*)c.beta0[2]};
     TIMED(&c, FVM_K_BETA, 1, launch_beta<double, double>(g, c.ph, (const double*)alpha, be[0], be[1], be[2], s));

@@ -177,7 +177,8 @@ __device__ __forceinline__ R sigma_r(R T, const PhysR<R>& q) {
 //   value = (d0 q0 s1 s2 + d1 q1 s0 s2 + d2 q2 s0 s1) / (d0 s1 s2 + d1 s0 s2 + d2 s0 s1);
 // the products grow like beta^2, far inside the double range.  In float they
 // would overflow once velocity jumps reach ~1e4, so float keeps the
-// reciprocal form, which underflows gracefully instead.
+// reciprocal form (which underflows gracefully instead) with the fast
+// approximate division: the weights need only a few correct digits.
 template <typename R>
 __device__ __forceinline__ R weno5(R vm2, R vm1, R v0, R vp1, R vp2, R eps) {
   const R c6 = R(1) / R(6);
@@ -198,8 +199,9 @@ __device__ __forceinline__ R weno5(R vm2, R vm1, R v0, R vp1, R vp2, R eps) {
     R w0 = R(0.1) * s1 * s2, w1 = R(0.6) * s0 * s2, w2 = R(0.3) * s0 * s1;
     return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
   } else {
-    R a0 = R(0.1) / s0, a1 = R(0.6) / s1, a2 = R(0.3) / s2;
-    return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+    // the weights only need a few correct digits: fast reciprocal division
+    R a0 = __fdividef(R(0.1), s0), a1 = __fdividef(R(0.6), s1), a2 = __fdividef(R(0.3), s2);
+    return __fdividef(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
   }
 }
 

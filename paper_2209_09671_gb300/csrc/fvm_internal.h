@@ -120,6 +120,8 @@ void launch_zero(T* a, long long n, cudaStream_t s);
 
 template <typename T>
 void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s);
+
+
 template <typename T>
 void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
 template <typename T>

@@ -75,10 +75,15 @@ void launch_sum_field(const T* a, long long n, bool squares, double* partial, do
   launch_sum_partials(partial, kRedBlocks, out, s);
 }
 
+// a -= sum / n, with the mean formed once per block (one double division per
+// block instead of per element)
 __global__ void k_sub_mean(double* __restrict__ a, long long n, const double* __restrict__ sum) {
+  __shared__ double mean;
+  if (threadIdx.x == 0) mean = (*sum) / (double)n;
+  __syncthreads();
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= n) return;
-  a[c] = a[c] - (*sum) / (double)n;
+  a[c] = a[c] - mean;
 }
 
 void launch_sub_mean(double* a, long long n, const double* sum, cudaStream_t s) {
@@ -346,6 +351,7 @@ __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* 
   __shared__ double sh[33];
   const float* be[3] = {b0, b1, b2};
   const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  const double wu = g.n[0] > 1 ? g.w[0] : (g.n[1] > 1 ? g.w[1] : g.w[2]);
   double acc = 0.0;
   for (long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x; cl < g.N;
        cl += (long long)gridDim.x * blockDim.x) {
@@ -354,18 +360,20 @@ __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* 
     decode_lv(g, c, i, j, k);
     const int idx[3] = {i, j, k};
     const double pc = p[c];
-    double Lp = 0.0;
+    // the fine level has cubic cells: one weight 1/h^2 for every coupled axis
+    double lsum = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int n = g.n[d];
       if (n == 1) continue;
       const int clo = idx[d] == 0 ? c + (n - 1) * st[d] : c - st[d];
       const int chi = idx[d] == n - 1 ? c - (n - 1) * st[d] : c + st[d];
-      const double blo = (double)be[d][c];
-      const double bhi = (g.bc[d] == WALL && idx[d] == n - 1) ? 0.0 : (double)be[d][chi];
-      Lp += (blo * (pc - p[clo]) + bhi * (pc - p[chi])) * g.w[d];
+      const float blo = be[d][c];
+      const float bhi = (g.bc[d] == WALL && idx[d] == n - 1) ? 0.f : be[d][chi];
+      lsum = fma((double)blo, pc - p[clo], lsum);
+      lsum = fma((double)bhi, pc - p[chi], lsum);
     }
-    const double r = b[c] - Lp;
+    const double r = fma(-wu, lsum, b[c]);
     r32[c] = (float)r;
     acc += r * r;
   }

@@ -140,33 +140,55 @@ enum { F_EVEN = 0, F_VEL = 1, F_TEMP = 2 };
 
 // stage one field into s: the boundary rules of the loaders are applied once
 // per staged point; points more than H cells outside the domain (ragged
-// tiles) are never read and hold 0
+// tiles) are never read and hold 0.  Threads walk rows of the tile: x from
+// threadIdx.x, one row (y, z) per (threadIdx.y, threadIdx.z) step.
 template <int H, int KIND, int C, typename R>
 __device__ __forceinline__ void stage(R* __restrict__ s, const R* __restrict__ a, const Geo& g,
                                       const TBC& tb) {
+  constexpr int SX = Tile<H>::SX, SY = Tile<H>::SY, SZ = Tile<H>::SZ;
   const bool in = tile_interior(g, H);
   const int x0 = blockIdx.x * kBX - H, y0 = blockIdx.y * kBY - H, z0 = blockIdx.z * kBZ - H;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  for (int e = flat_tid(); e < Tile<H>::N; e += kThreads) {
-    const int lx = e % Tile<H>::SX;
-    const int t = e / Tile<H>::SX;
-    const int ly = t % Tile<H>::SY;
-    const int lz = t / Tile<H>::SY;
-    const int i = x0 + lx, j = y0 + ly, k = z0 + lz;
-    R v;
+  const int tx = threadIdx.x;
+  for (int row = threadIdx.y + kBY * threadIdx.z; row < SY * SZ; row += kBY * kBZ) {
+    const int ly = row % SY, lz = row / SY;
+    const int j = y0 + ly, k = z0 + lz;
+    R* __restrict__ srow = s + row * SX;
     if (in) {
-      v = __ldg(a + ((k * ny + j) * nx + i));
-    } else if (i < -H || i > nx - 1 + H || j < -H || j > ny - 1 + H || k < -H || k > nz - 1 + H) {
-      v = R(0);
-    } else if (KIND == F_EVEN) {
-      v = ld_even(a, g, i, j, k);
-    } else if (KIND == F_VEL) {
-      v = ld_vel<C>(a, g, i, j, k);
+      const R* __restrict__ arow = a + ((k * ny + j) * nx + x0);
+#pragma unroll
+      for (int lx = tx; lx < SX; lx += kBX) srow[lx] = __ldg(arow + lx);
     } else {
-      v = ld_T(a, g, tb, i, j, k);
+      const bool rowout = j < -H || j > ny - 1 + H || k < -H || k > nz - 1 + H;
+      for (int lx = tx; lx < SX; lx += kBX) {
+        const int i = x0 + lx;
+        R v;
+        if (rowout || i < -H || i > nx - 1 + H) v = R(0);
+        else if (KIND == F_EVEN) v = ld_even(a, g, i, j, k);
+        else if (KIND == F_VEL) v = ld_vel<C>(a, g, i, j, k);
+        else v = ld_T(a, g, tb, i, j, k);
+        srow[lx] = v;
+      }
     }
-    s[e] = v;
   }
+}
+
+// single loads for the few values a kernel does not stage: direct in an
+// interior tile, through the boundary loaders otherwise
+template <typename R>
+__device__ __forceinline__ R g_even(const R* __restrict__ a, const Geo& g, bool in, int i, int j,
+                                    int k) {
+  return in ? __ldg(a + ((k * g.n[1] + j) * g.n[0] + i)) : ld_even(a, g, i, j, k);
+}
+template <int C, typename R>
+__device__ __forceinline__ R g_vel(const R* __restrict__ a, const Geo& g, bool in, int i, int j,
+                                   int k) {
+  return in ? __ldg(a + ((k * g.n[1] + j) * g.n[0] + i)) : ld_vel<C>(a, g, i, j, k);
+}
+template <typename R>
+__device__ __forceinline__ R g_T(const R* __restrict__ a, const Geo& g, const TBC& tb, bool in,
+                                 int i, int j, int k) {
+  return in ? __ldg(a + ((k * g.n[1] + j) * g.n[0] + i)) : ld_T(a, g, tb, i, j, k);
 }
 
 template <int A>
@@ -193,44 +215,44 @@ template <int HI, int HO, typename R>
 __device__ __forceinline__ void smooth_pass(const Geo& g, const R* __restrict__ in,
                                             R* __restrict__ out) {
   const bool sx = g.n[0] > 1, sy = g.n[1] > 1, sz = g.n[2] > 1;
-  for (int e = flat_tid(); e < Tile<HO>::N; e += kThreads) {
-    const int lx = e % Tile<HO>::SX - HO;
-    const int t = e / Tile<HO>::SX;
-    const int ly = t % Tile<HO>::SY - HO;
-    const int lz = t / Tile<HO>::SY - HO;
-    R acc = 0;
+  constexpr int SX = Tile<HO>::SX, SY = Tile<HO>::SY, SZ = Tile<HO>::SZ;
+  for (int row = threadIdx.y + kBY * threadIdx.z; row < SY * SZ; row += kBY * kBZ) {
+    const int ly = row % SY - HO, lz = row / SY - HO;
+    for (int ex = threadIdx.x; ex < SX; ex += kBX) {
+      const int lx = ex - HO;
+      R acc = 0;
 #pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-      if (!sz && dz != 0) continue;
-      const R wz = sz ? (dz == 0 ? R(0.5) : R(0.25)) : R(1);
-      R accy = 0;
+      for (int dz = -1; dz <= 1; ++dz) {
+        if (!sz && dz != 0) continue;
+        const R wz = sz ? (dz == 0 ? R(0.5) : R(0.25)) : R(1);
+        R accy = 0;
 #pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        if (!sy && dy != 0) continue;
-        const R wy = sy ? (dy == 0 ? R(0.5) : R(0.25)) : R(1);
-        R accx = 0;
+        for (int dy = -1; dy <= 1; ++dy) {
+          if (!sy && dy != 0) continue;
+          const R wy = sy ? (dy == 0 ? R(0.5) : R(0.25)) : R(1);
+          R accx = 0;
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          if (!sx && dx != 0) continue;
-          const R wx = sx ? (dx == 0 ? R(0.5) : R(0.25)) : R(1);
-          accx += wx * in[Tile<HI>::at(lx + dx, ly + dy, lz + dz)];
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (!sx && dx != 0) continue;
+            const R wx = sx ? (dx == 0 ? R(0.5) : R(0.25)) : R(1);
+            accx += wx * in[Tile<HI>::at(lx + dx, ly + dy, lz + dz)];
+          }
+          accy += wy * accx;
         }
-        accy += wy * accx;
+        acc += wz * accy;
       }
-      acc += wz * accy;
+      out[row * SX + ex] = acc;
     }
-    out[e] = acc;
   }
 }
 
 template <int HI, int HO, typename R>
 __device__ __forceinline__ void copy_tile(const R* __restrict__ in, R* __restrict__ out) {
-  for (int e = flat_tid(); e < Tile<HO>::N; e += kThreads) {
-    const int lx = e % Tile<HO>::SX - HO;
-    const int t = e / Tile<HO>::SX;
-    const int ly = t % Tile<HO>::SY - HO;
-    const int lz = t / Tile<HO>::SY - HO;
-    out[e] = in[Tile<HI>::at(lx, ly, lz)];
+  constexpr int SX = Tile<HO>::SX, SY = Tile<HO>::SY, SZ = Tile<HO>::SZ;
+  for (int row = threadIdx.y + kBY * threadIdx.z; row < SY * SZ; row += kBY * kBZ) {
+    const int ly = row % SY - HO, lz = row / SY - HO;
+    for (int ex = threadIdx.x; ex < SX; ex += kBX)
+      out[row * SX + ex] = in[Tile<HI>::at(ex - HO, ly, lz)];
   }
 }
 
@@ -344,15 +366,14 @@ template <typename R>
 struct ScalShared {
   R a[Tile<3>::N];
   R T[Tile<3>::N];
-  R u[3][Tile<1>::N];
   ScalFlux<R> F;
 };
 
 // advective fluxes of alpha and T and the conductive flux of T through the
 // low D-face of local cell (lx,ly,lz)
 template <int D, typename R>
-__device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<R>& ph, int lx,
-                                            int ly, int lz, R& Fa, R& FT, R& Df) {
+__device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<R>& ph, const R Uf,
+                                            int lx, int ly, int lz, R& Fa, R& FT, R& Df) {
   const int dx = D == 0, dy = D == 1, dz = D == 2;
   R av[6], tv[6];
 #pragma unroll
@@ -361,7 +382,6 @@ __device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<
     av[m] = S.a[Tile<3>::at(lx + o * dx, ly + o * dy, lz + o * dz)];
     tv[m] = S.T[Tile<3>::at(lx + o * dx, ly + o * dy, lz + o * dz)];
   }
-  const R Uf = S.u[D][Tile<1>::at(lx, ly, lz)];
   Fa = upwind_flux(Uf, av, ph.eps_a);
   FT = upwind_flux(Uf, tv, ph.eps_T);
   R lL = mixr(av[2], ph.lam), lR = mixr(av[3], ph.lam);
@@ -377,9 +397,7 @@ __global__ void __launch_bounds__(kThreads)
   ScalShared<R>& S = *reinterpret_cast<ScalShared<R>*>(smem_raw);
   stage<3, F_EVEN, 0>(S.a, X.alpha, g, tb);
   stage<3, F_TEMP, 0>(S.T, X.T, g, tb);
-  stage<1, F_VEL, 0>(S.u[0], X.u[0], g, tb);
-  stage<1, F_VEL, 1>(S.u[1], X.u[1], g, tb);
-  stage<1, F_VEL, 2>(S.u[2], X.u[2], g, tb);
+  const bool in = tile_interior(g, 3);
   __syncthreads();
   const R dt = (R)dtp[0];
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
@@ -388,21 +406,21 @@ __global__ void __launch_bounds__(kThreads)
   const R ih = ph.ih;
   ScalFlux<R>& F = S.F;
   if (i <= nx && j < ny && k < nz) {
-    scalar_face<0>(S, ph, tx, ty, tz, F.x[0][tz][ty][tx], F.x[1][tz][ty][tx], F.x[2][tz][ty][tx]);
+    scalar_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i, j, k), tx, ty, tz, F.x[0][tz][ty][tx], F.x[1][tz][ty][tx], F.x[2][tz][ty][tx]);
     if (tx == kBX - 1 && i + 1 <= nx)
-      scalar_face<0>(S, ph, tx + 1, ty, tz, F.x[0][tz][ty][tx + 1], F.x[1][tz][ty][tx + 1],
+      scalar_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i + 1, j, k), tx + 1, ty, tz, F.x[0][tz][ty][tx + 1], F.x[1][tz][ty][tx + 1],
                      F.x[2][tz][ty][tx + 1]);
   }
   if (i < nx && j <= ny && k < nz) {
-    scalar_face<1>(S, ph, tx, ty, tz, F.y[0][tz][ty][tx], F.y[1][tz][ty][tx], F.y[2][tz][ty][tx]);
+    scalar_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j, k), tx, ty, tz, F.y[0][tz][ty][tx], F.y[1][tz][ty][tx], F.y[2][tz][ty][tx]);
     if (ty == kBY - 1 && j + 1 <= ny)
-      scalar_face<1>(S, ph, tx, ty + 1, tz, F.y[0][tz][ty + 1][tx], F.y[1][tz][ty + 1][tx],
+      scalar_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j + 1, k), tx, ty + 1, tz, F.y[0][tz][ty + 1][tx], F.y[1][tz][ty + 1][tx],
                      F.y[2][tz][ty + 1][tx]);
   }
   if (i < nx && j < ny && k <= nz) {
-    scalar_face<2>(S, ph, tx, ty, tz, F.z[0][tz][ty][tx], F.z[1][tz][ty][tx], F.z[2][tz][ty][tx]);
+    scalar_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k), tx, ty, tz, F.z[0][tz][ty][tx], F.z[1][tz][ty][tx], F.z[2][tz][ty][tx]);
     if (tz == kBZ - 1 && k + 1 <= nz)
-      scalar_face<2>(S, ph, tx, ty, tz + 1, F.z[0][tz + 1][ty][tx], F.z[1][tz + 1][ty][tx],
+      scalar_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k + 1), tx, ty, tz + 1, F.z[0][tz + 1][ty][tx], F.z[1][tz + 1][ty][tx],
                      F.z[2][tz + 1][ty][tx]);
   }
   __syncthreads();
@@ -468,10 +486,6 @@ template <typename R>
 struct MomShared {
   R u[3][Tile<3>::N];     // velocity components
   R mu[Tile<1>::N];       // cell viscosity mu(alpha)
-  R a[Tile<1>::N];        // alpha
-  R T[Tile<1>::N];
-  R kap[Tile<1>::N];
-  R M[3][Tile<1>::N];
   MomFlux<R> F;
 };
 
@@ -538,9 +552,10 @@ __device__ __forceinline__ void edge_flux(const MomShared<R>& S, const PhysR<R>&
 }
 
 template <int D, typename R>
-__device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>& ph,
-                                                   MomShared<R>& S, const R* __restrict__ u_old,
-                                                   R* __restrict__ us, R dt) {
+__device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>& ph, const TBC& tb,
+                                                   const Fields<R>& X, const R* __restrict__ kappa,
+                                                   const R* __restrict__ MD, bool in,
+                                                   MomShared<R>& S, R* __restrict__ us, R dt) {
   constexpr int t1 = Tang<D>::t1, t2 = Tang<D>::t2;
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
@@ -602,16 +617,15 @@ __device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>&
         V += (F.v[2][z][y][x] - F.v[2][tz][ty][tx]) * ih;
       }
       // forces on the face between cell L = c - e_D and R = c
-      int x = tx, y = ty, z = tz;
-      sh1<D>(x, y, z, -1);
-      const int cl = Tile<1>::at(x, y, z), cr = Tile<1>::at(tx, ty, tz);
-      const R alL = S.a[cl], alR = S.a[cr];
+      int a = i, b = j, cc = k;
+      sh1<D>(a, b, cc, -1);
+      const R alL = g_even(X.alpha, g, in, a, b, cc), alR = X.alpha[c];
       const R rho_f = R(0.5) * (mixr(alL, ph.rho) + mixr(alR, ph.rho));
-      const R sig_f = R(0.5) * (sigma_r(S.T[cl], ph) + sigma_r(S.T[cr], ph));
-      const R kap_f = R(0.5) * (S.kap[cl] + S.kap[cr]);
+      const R sig_f = R(0.5) * (sigma_r(g_T(X.T, g, tb, in, a, b, cc), ph) + sigma_r(X.T[c], ph));
+      const R kap_f = R(0.5) * (g_even(kappa, g, in, a, b, cc) + kappa[c]);
       const R jump = (alR - alL) * ih;
       const R fn = -sig_f * kap_f * jump;
-      const R fM = R(0.5) * (S.M[D][cl] + S.M[D][cr]);
+      const R fM = R(0.5) * (g_even(MD, g, in, a, b, cc) + MD[c]);
       us[c] = S.u[D][Tile<3>::at(tx, ty, tz)] + dt * (A + (V + fn + fM) / rho_f + ph.g[D]);
     }
   }
@@ -629,19 +643,15 @@ __global__ void __launch_bounds__(kThreads)
   stage<3, F_VEL, 0>(S.u[0], X.u[0], g, tb);
   stage<3, F_VEL, 1>(S.u[1], X.u[1], g, tb);
   stage<3, F_VEL, 2>(S.u[2], X.u[2], g, tb);
-  stage<1, F_EVEN, 0>(S.a, X.alpha, g, tb);
-  stage<1, F_TEMP, 0>(S.T, X.T, g, tb);
-  stage<1, F_EVEN, 0>(S.kap, kappa, g, tb);
-  stage<1, F_EVEN, 0>(S.M[0], M0, g, tb);
-  stage<1, F_EVEN, 0>(S.M[1], M1, g, tb);
-  stage<1, F_EVEN, 0>(S.M[2], M2, g, tb);
+  stage<1, F_EVEN, 0>(S.mu, X.alpha, g, tb);
   __syncthreads();
-  for (int e = flat_tid(); e < Tile<1>::N; e += kThreads) S.mu[e] = mixr(S.a[e], ph.mu);
+  for (int e = flat_tid(); e < Tile<1>::N; e += kThreads) S.mu[e] = mixr(S.mu[e], ph.mu);
   __syncthreads();
   const R dt = (R)dtp[0];
-  momentum_component<0>(g, ph, S, X.u[0], us0, dt);
-  momentum_component<1>(g, ph, S, X.u[1], us1, dt);
-  momentum_component<2>(g, ph, S, X.u[2], us2, dt);
+  const bool in = tile_interior(g, 3);
+  momentum_component<0>(g, ph, tb, X, kappa, M0, in, S, us0, dt);
+  momentum_component<1>(g, ph, tb, X, kappa, M1, in, S, us1, dt);
+  momentum_component<2>(g, ph, tb, X, kappa, M2, in, S, us2, dt);
 }
 
 template <typename R>

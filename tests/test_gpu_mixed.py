@@ -86,3 +86,25 @@ def test_mixed_melt_pool_small():
     errs = {k: rel_l2(out[k], ref[k].numpy()) for k in FIELDS}
     assert errs["alpha"] <= 1e-6 and errs["T"] <= 1e-6, errs
     assert max(errs["u"], errs["v"], errs["w"], errs["p"]) <= 1e-4, errs
+
+
+def test_mixed_steps_replayed_as_graphs_match_eager_launches():
+    """On a non-default stream the refinement iteration is captured once and
+    replayed as a CUDA graph; the result is bitwise that of eager launches
+    (same kernels, same order)."""
+    P = need_gpu()
+    p, s = cases.melt_pool(32, 32, 32, precision=cases.MIXED)
+    outs = []
+    for use_stream in (False, True):
+        stream = torch.cuda.Stream() if use_stream else None
+        ctx = torch.cuda.stream(stream) if use_stream else torch.cuda.stream(torch.cuda.current_stream())
+        with ctx:
+            solver = P.Solver(p, stream=stream)
+            dev = P.to_device(s, True)
+            for n in range(3):
+                solver.fvm_step(dev, n, 0.0)
+            torch.cuda.synchronize()
+            outs.append({k: v.clone() for k, v in dev.items()})
+            solver.close()
+    for k in FIELDS:
+        assert torch.equal(outs[0][k], outs[1][k]), k
