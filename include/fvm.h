@@ -163,6 +163,17 @@ fvm_status fvm_poisson_solve_noalloc(const fvm_params* prm, const void* alpha,
                                      const double* rhs, double* p, void* cuda_stream,
                                      fvm_step_info* info);
 
+/* The first forward-Euler stage without its projection, for testing the
+ * stage-local operators at full size: smoothing, normals, curvature and
+ * Marangoni vector (Sec. III, Eq. 2-5), WENO5 transport of alpha (Eq. 1) and
+ * T with conduction and the surface heat flux, and the momentum predictor.
+ * X: device state (p unused); dt > 0; heat-source centre at step_index.
+ * ustar[3]: device outputs u*, v*, w* (working precision); alpha_out, T_out:
+ * device outputs alpha + dt R_alpha and T + dt R_T.  Outputs must not alias
+ * the inputs.  Uses the context's workspace. */
+fvm_status fvm_stage_predict(fvm_ctx* ctx, const fvm_state* X, long step_index, double dt,
+                             void* const ustar[3], void* alpha_out, void* T_out);
+
 /* Reverse-mode (adjoint) of one step: not implemented in this library yet;
  * returns FVM_EUNSUPPORTED. */
 fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index,

@@ -815,6 +815,46 @@ fvm_status fvm_poisson_solve(fvm_ctx* ctx, const void* alpha, const double* rhs,
   return cuda_check(ctx, "poisson");
 }
 
+}  // extern "C"
+
+namespace {
+template <typename R>
+fvm_status predict_impl(fvm_ctx* c, const fvm_state* X_, long step_index, double dt,
+                        void* const* ustar, void* alpha_out, void* T_out) {
+  cudaStream_t s = c->stream;
+  const Geo& g = c->g;
+  void* xp[5] = {X_->u, X_->v, X_->w, X_->alpha, X_->T};
+  Fields<R> X = fields_of<R>(xp);
+  Fields<R> Y = X;
+  Y.alpha = (R*)alpha_out;
+  Y.T = (R*)T_out;
+  TIMED(c, FVM_K_DT, 1, launch_set_scalar(c->dt_dev, dt, s));
+  const double xc = c->prm.q_x0 + c->prm.q_speed * c->prm.h * (double)step_index;
+  R* M[3] = {(R*)c->M[0], (R*)c->M[1], (R*)c->M[2]};
+  TIMED(c, FVM_K_INTERFACE, 1, launch_interface<R>(g, c->ph, c->tb, c->prm.smooth_passes, X.alpha,
+                                                X.T, (R*)c->kappa, M[0], M[1], M[2], s));
+  TIMED(c, FVM_K_SCALARS, 1, launch_scalars<R>(g, c->ph, c->tb, X, X, Y, c->dt_dev, 0.0, 1.0, xc, s));
+  TIMED(c, FVM_K_MOMENTUM, 1, launch_momentum<R>(g, c->ph, c->tb, X, (R*)c->kappa, M[0], M[1], M[2],
+                                              (R*)ustar[0], (R*)ustar[1], (R*)ustar[2], c->dt_dev, s));
+  return cuda_check(c, "stage predictor");
+}
+}  // namespace
+
+extern "C" fvm_status fvm_stage_predict(fvm_ctx* ctx, const fvm_state* X, long step_index,
+                                        double dt, void* const ustar[3], void* alpha_out,
+                                        void* T_out) {
+  if (!ctx) return FVM_EINVAL;
+  if (!X || !X->u || !X->v || !X->w || !X->alpha || !X->T || !ustar || !ustar[0] || !ustar[1] ||
+      !ustar[2] || !alpha_out || !T_out)
+    return set_err(ctx, FVM_EINVAL, "null pointer");
+  if (!(dt > 0.0)) return set_err(ctx, FVM_EINVAL, "dt must be > 0");
+  cudaGetLastError();
+  if (ctx->mixed) return predict_impl<float>(ctx, X, step_index, dt, ustar, alpha_out, T_out);
+  return predict_impl<double>(ctx, X, step_index, dt, ustar, alpha_out, T_out);
+}
+
+extern "C" {
+
 fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index, double dt,
                             const fvm_state* lam_np1, fvm_state* lam_n, double dtheta[2]) {
   (void)st_n; (void)step_index; (void)dt; (void)lam_np1; (void)lam_n; (void)dtheta;

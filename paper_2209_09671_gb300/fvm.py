@@ -64,7 +64,8 @@ class fvm_step_info(ctypes.Structure):
 
 EXPORTS = ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step", "fvm_poisson_solve",
            "fvm_step_adjoint", "fvm_status_string", "fvm_last_error", "fvm_version",
-           "fvm_profile", "fvm_profile_read", "fvm_launch_count", "fvm_poisson_solve_noalloc")
+           "fvm_profile", "fvm_profile_read", "fvm_launch_count", "fvm_poisson_solve_noalloc",
+           "fvm_stage_predict")
 
 KERNEL_CLASSES = ("smooth", "interface", "scalars", "momentum", "div_rhs", "beta", "gs_fine",
                   "gs_coarse", "restrict_fine", "restrict_coarse", "prolong_fine",
@@ -102,13 +103,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fvm_version.restype = ctypes.c_char_p
     lib.fvm_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.fvm_launch_count.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_long)]
+    lib.fvm_stage_predict.argtypes = [ctypes.c_void_p, P(fvm_state), ctypes.c_long,
+                                      ctypes.c_double, P(ctypes.c_void_p), ctypes.c_void_p,
+                                      ctypes.c_void_p]
     lib.fvm_poisson_solve_noalloc.argtypes = [P(fvm_params), ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, P(fvm_step_info)]
     lib.fvm_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_long),
                                      P(ctypes.c_double)]
     for name in ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step",
                  "fvm_poisson_solve", "fvm_step_adjoint", "fvm_profile", "fvm_profile_read", "fvm_launch_count",
-                 "fvm_poisson_solve_noalloc"):
+                 "fvm_poisson_solve_noalloc", "fvm_stage_predict"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -223,6 +227,20 @@ class Solver:
             self._check(rc, "fvm_poisson_solve")
         out = inf.as_dict()
         out["status"] = rc
+        return out
+
+    def fvm_stage_predict(self, state: dict, step_index: int, dt: float) -> dict:
+        """The first stage's predictor (no projection): returns u*, v*, w* and
+        alpha + dt R_alpha, T + dt R_T as new tensors."""
+        import torch
+        st = self._state(state)
+        out = {k: torch.empty_like(state[k]) for k in ("u", "v", "w", "alpha", "T")}
+        us = (ctypes.c_void_p * 3)(out["u"].data_ptr(), out["v"].data_ptr(), out["w"].data_ptr())
+        rc = self.lib.fvm_stage_predict(self.ctx, ctypes.byref(st), ctypes.c_long(step_index),
+                                        ctypes.c_double(dt), us,
+                                        ctypes.c_void_p(out["alpha"].data_ptr()),
+                                        ctypes.c_void_p(out["T"].data_ptr()))
+        self._check(rc, "fvm_stage_predict")
         return out
 
     def fvm_step_adjoint(self, state_n, step_index, dt, lam_np1, lam_n):
