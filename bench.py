@@ -77,6 +77,14 @@ def parse():
     ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="instead: the FP64 adjoint workload (gradient of the interface-height "
+                         "objective through a checkpointed rollout, and the adjoint step's cost)")
+    ap.add_argument("--adj-n", type=int, default=192, help="adjoint workload: cells per axis")
+    ap.add_argument("--adj-steps", type=int, default=200, help="adjoint workload: rollout steps")
+    ap.add_argument("--adj-every", type=int, default=20, help="adjoint workload: checkpoint interval")
+    ap.add_argument("--fd", action="store_true",
+                    help="adjoint workload: also central differences in theta (4 more rollouts)")
     return ap.parse_args()
 
 
@@ -201,6 +209,137 @@ def run_reference(args, rank, world):
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def adjoint_workload(n):
+    """The thermocapillary channel physics (equal unit properties, Dirichlet
+    cos(2 pi x/L) bottom wall) at n x n x n with a stationary Gaussian surface
+    source and a rippled interface, FP64, projections to 1e-11 (about ten
+    times the FP64 rounding floor of the residual of smooth modes at 192^3);
+    the objective is the squared deviation of the column interface heights
+    from a rippled target."""
+    import numpy as np
+
+    import cases
+    p, s = cases.adjoint_channel(nx=n, ny=n, nz=n)
+    p = p.replace(precision=cases.F64, mg_rtol=1e-11, mg_max_cycles=200, adjoint=1)
+    x = cases.cell_centres(p)[0]
+    H0 = s["alpha"].sum(axis=0) * p.h
+    target = H0 + 0.02 * np.cos(2 * np.pi * np.broadcast_to(x, p.shape)[0] / (p.nx * p.h))
+    return p, s, target
+
+
+def run_adjoint(args, rank, world, local_rank):
+    """One JSON line: cost of fvm_step_adjoint against fvm_step at the same
+    size, and the gradient dJ/dtheta of the interface-height objective after
+    --adj-steps steps (checkpoint every --adj-every), optionally checked
+    against central differences of the forward rollout."""
+    import torch
+
+    import paper_2209_09671_gb300 as P
+    from paper_2209_09671_gb300 import adjoint as ADJ
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p, s0, target_np = adjoint_workload(args.adj_n)
+    target = torch.tensor(target_np, device=dev)
+    N = p.nx * p.ny * p.nz
+    stream = torch.cuda.Stream(device=dev)
+
+    def J_of(alpha):
+        H = alpha.sum(dim=0) * p.h
+        return ((H - target) ** 2).sum() * p.h * p.h
+
+    with torch.cuda.stream(stream):
+        solver = P.Solver(p, device=dev, stream=stream)
+        state = P.to_device(s0, False, dev)
+        info = solver.fvm_step({k: v.clone() for k, v in state.items()}, 0, 0.0)
+        dt = info["dt"]
+        dts = [dt] * args.adj_steps
+        # forward step and adjoint step, timed with events on the solver's stream
+        work = {k: v.clone() for k, v in state.items()}
+        for q in range(2):
+            solver.fvm_step(work, q, dt, info=False)
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for q in range(reps):
+            solver.fvm_step(work, 2 + q, dt, info=False)
+        e1.record(stream)
+        stream.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / reps
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(20220919)
+        lam = {k: torch.rand(work[k].shape, generator=gen, dtype=torch.float64, device=dev) - 0.5
+               for k in P.fvm.FIELDS5}
+        lam_out = {k: torch.empty_like(work[k]) for k in P.fvm.FIELDS5}
+        solver.fvm_step_adjoint(work, 5, dt, lam, lam_out)
+        solver.fvm_launch_count(reset=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for q in range(reps):
+            solver.fvm_step_adjoint(work, 5, dt, lam, lam_out)
+        e1.record(stream)
+        stream.synchronize()
+        adj_ms = e0.elapsed_time(e1) / reps
+        adj_launches = solver.fvm_launch_count() / reps
+        solver.fvm_profile(True)
+        solver.fvm_step_adjoint(work, 5, dt, lam, lam_out)
+        prof = solver.fvm_profile_read()
+        solver.fvm_profile(False)
+        del work, lam, lam_out
+        # the gradient through the rollout (checkpointing + recomputation)
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        theta = torch.tensor([p.dsigma_dT, p.q_power], dtype=torch.float64, device=dev,
+                             requires_grad=True)
+        ins = {k: state[k].clone().requires_grad_(k != "p") for k in ADJ.STATE_KEYS}
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = ADJ.Rollout.apply(solver, 0, dts, theta,
+                                *(ins[k] for k in P.fvm.FIELDS5), ins["p"])
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        J = J_of(out[3])
+        J.backward()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        clk = clocks.stop()
+        grad = theta.grad.tolist()
+        line = {"metric": "adjoint step cost and rollout gradient, FP64",
+                "unit": "ms", "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"thermocapillary channel + Gaussian source "
+                                       f"{p.nx}x{p.ny}x{p.nz}, FP64, projections to 1e-11",
+                           "cells": N, "dt": dt, "rollout_steps": args.adj_steps,
+                           "checkpoint_every": args.adj_every},
+                "forward_step_ms": fwd_ms, "adjoint_step_ms": adj_ms,
+                "adjoint_over_forward": adj_ms / fwd_ms,
+                "adjoint_launches_per_step": adj_launches,
+                "adjoint_profile_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
+                "J": J.item(), "dJ_dtheta": grad,
+                "rollout_forward_s": t1 - t0, "rollout_backward_s": t2 - t1,
+                "backward_over_forward": (t2 - t1) / (t1 - t0),
+                "clocks": clk}
+        if args.fd:
+            fd = []
+            for q, name in enumerate(("dsigma_dT", "q_power")):
+                v = getattr(p, name)
+                eps = 1e-4 * abs(v)
+                Js = []
+                for sgn in (1, -1):
+                    sv = P.Solver(p.replace(adjoint=0, **{name: v + sgn * eps}), device=dev,
+                                  stream=stream)
+                    st = {k: x.clone() for k, x in state.items()}
+                    ADJ.rollout(sv, st, 0, dts)
+                    Js.append(J_of(st["alpha"]).item())
+                    sv.close()
+                    del st
+                fd.append((Js[0] - Js[1]) / (2 * eps))
+            line["fd"] = {"eps_rel": 1e-4, "dJ_dtheta": fd,
+                          "rel_err": [abs(a - b) / abs(b) for a, b in zip(grad, fd)]}
     print(json.dumps(line), flush=True)
 
 
@@ -413,6 +552,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.adjoint:
+        run_adjoint(args, rank, world, local_rank)
         return
     if world > 1:
         import torch

@@ -113,6 +113,7 @@ class Params:
     coarse_maxit: int = 1000
     precision: int = F64
     mx_inner_cycles: int = 2
+    adjoint: int = 0
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
@@ -256,6 +257,26 @@ def smooth_noise(seed: int, shape, corr_cells: float = 8.0) -> np.ndarray:
     F *= np.exp(-K2 * (corr_cells / 2.0) ** 2)
     out = np.fft.irfftn(F, s=shape, axes=tuple(range(len(shape))))
     return out / np.abs(out).max()
+
+
+def adjoint_channel(nx: int = 32, ny: int = 32, nz: int = 16, dT: float = 1.0,
+                    sigmaT: float = 0.01, q_power: float = 0.05):
+    """The thermocapillary channel physics (equal unit properties, Dirichlet
+    cos(2 pi x / L) bottom wall) with a stationary Gaussian surface source of
+    radius 8 cells at the centre of the interface; the interface carries a
+    small seeded ripple so that curvature, Marangoni and WENO terms are all
+    active.  Used for gradients with respect to theta = (dsigma/dT, q_power)."""
+    p, s = thermocapillary_channel(nx=nx, ny=ny, nz=nz, dT=dT, sigmaT=sigmaT)
+    h = p.h
+    p = p.replace(q_power=q_power, q_radius=8.0 * h, q_x0=0.5 * nx * h, q_y0=0.5 * ny * h,
+                  q_speed=0.0)
+    x, y, z = cell_centres(p)
+    r = uniform(SEED + 7, (4,), 0.0, 1.0)
+    Lx, Ly = nx * h, ny * h
+    zi = 0.5 * nz * h + 0.6 * h * (np.cos(2 * math.pi * x / Lx + 6.283 * r[0]) *
+                                    np.cos(2 * math.pi * y / Ly + 6.283 * r[1]))
+    s["alpha"][:] = np.broadcast_to(0.5 * (1.0 - np.tanh((z - zi) / (1.2 * h))), p.shape)
+    return p, s
 
 
 def random_smooth_state(p: Params, seed: int = SEED, amp_u: float = 1.0,

@@ -84,6 +84,8 @@ typedef struct {
   double coarse_rtol; int coarse_maxit;    /* CG on the coarsest level            */
   int precision;                           /* fvm_precision                       */
   int mx_inner_cycles;                     /* float V-cycles per double refinement */
+  int adjoint;                             /* 1: also reserve the buffers of      */
+                                           /* fvm_step_adjoint (F64 only)        */
 } fvm_params;
 
 /* Caller-owned device fields of one state. u, v, w, alpha, T: double (F64) or
@@ -174,8 +176,25 @@ fvm_status fvm_poisson_solve_noalloc(const fvm_params* prm, const void* alpha,
 fvm_status fvm_stage_predict(fvm_ctx* ctx, const fvm_state* X, long step_index, double dt,
                              void* const ustar[3], void* alpha_out, void* T_out);
 
-/* Reverse-mode (adjoint) of one step: not implemented in this library yet;
- * returns FVM_EUNSUPPORTED. */
+/* Reverse mode of one FP64 step at a given dt (the discrete adjoint that a
+ * gradient-based calibration of the Sec. III model needs; the paper itself
+ * differentiates nothing, so the entry point extends it).  With
+ * S_{n+1} = Step(S_n; theta), theta = (dsigma_dT, q_power), it returns
+ *   lam_n     = (dS_{n+1}/dS_n)^T lam_np1           (u, v, w, alpha, T)
+ *   dtheta[q] = (dS_{n+1}/dtheta_q)^T lam_np1       (added to dtheta)
+ * st_n: the state before the step (device, double; read only, p is the
+ * warm start of the recomputed projections); lam_np1 (read only) and lam_n
+ * (written, must not alias lam_np1): device double fields, layout as the
+ * state; their p members are ignored.  dtheta: host, 2 doubles, ACCUMULATED
+ * into (the caller zeroes them).  The stages are recomputed from st_n; the
+ * three projections are adjoined by the same multigrid solve (the operator
+ * is symmetric for constant beta).  Requirements, else an error and no
+ * write: a context created with adjoint = 1 and precision F64 (EINVAL /
+ * EUNSUPPORTED), equal rho, mu, cp and lambda in both phases
+ * (EUNSUPPORTED: the projection coefficient and the transport coefficients
+ * are then constant), dt > 0 (EINVAL).  The derivative of |g| at g = 0 is
+ * taken as 0.  Entries of lam_n on wall faces are 0.  Synchronises the
+ * context's stream. */
 fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index,
                             double dt, const fvm_state* lam_np1, fvm_state* lam_n,
                             double dtheta[2]);
@@ -193,7 +212,7 @@ typedef enum {
   FVM_K_BETA, FVM_K_GS_FINE, FVM_K_GS_COARSE, FVM_K_RESTRICT_FINE, FVM_K_RESTRICT_COARSE,
   FVM_K_PROLONG_FINE, FVM_K_PROLONG_COARSE, FVM_K_COARSE_CG, FVM_K_RESNORM,
   FVM_K_RESIDUAL64, FVM_K_ADD_CORRECTION, FVM_K_CORRECT, FVM_K_DT, FVM_K_DIAGNOSTICS,
-  FVM_K_MISC, FVM_KCLASS_COUNT
+  FVM_K_MISC, FVM_K_ADJOINT, FVM_KCLASS_COUNT
 } fvm_kernel_class;
 
 fvm_status fvm_profile(fvm_ctx* ctx, int on);

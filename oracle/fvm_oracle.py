@@ -56,6 +56,14 @@ def _t(a):
     return torch.as_tensor(a, dtype=DT)
 
 
+def norm3(x):
+    """sqrt(x) for the squared length of a gradient; equal to torch.sqrt in
+    value, with the derivative at x = 0 taken as 0 (|g| has no gradient where
+    g vanishes, e.g. away from the interface)."""
+    pos = x > 0.0
+    return torch.where(pos, torch.sqrt(torch.where(pos, x, torch.ones_like(x))), torch.zeros_like(x))
+
+
 # ==========================================================================
 # Grid helpers
 # ==========================================================================
@@ -332,7 +340,7 @@ def face_normal_component(At, grid, d, eps_n, s=0):
         gt = ((Sd(At, grid, (t, 1), (d, s)) - Sd(At, grid, (t, -1), (d, s)))
               + (Sd(At, grid, (t, 1), (d, s - 1)) - Sd(At, grid, (t, -1), (d, s - 1)))) / (4.0 * h)
         sq = sq + gt * gt
-    return gd / (torch.sqrt(sq) + eps_n)
+    return gd / (norm3(sq) + eps_n)
 
 
 def curvature(alpha_s, grid):
@@ -364,8 +372,8 @@ def marangoni_vector(Ap, Asp, sigP, grid):
     g = central_grad(Ap, grid)
     t = central_grad(Asp, grid)
     s = central_grad(sigP, grid)
-    gn = torch.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2)
-    tn = torch.sqrt(t[0] ** 2 + t[1] ** 2 + t[2] ** 2) + eps_n
+    gn = norm3(g[0] ** 2 + g[1] ** 2 + g[2] ** 2)
+    tn = norm3(t[0] ** 2 + t[1] ** 2 + t[2] ** 2) + eps_n
     nh = [t[d] / tn for d in range(3)]
     ns = nh[0] * s[0] + nh[1] * s[1] + nh[2] * s[2]
     return [gn * (s[d] - nh[d] * ns) for d in range(3)], gn

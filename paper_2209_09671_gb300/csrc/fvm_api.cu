@@ -105,6 +105,8 @@ const char* check_params(const fvm_params* p) {
   if (!(p->weno_eps > 0.0)) return "weno_eps must be > 0";
   if (p->smooth_passes > 2) return "smooth_passes above 2 is not supported";
   if (p->q_power != 0.0 && !(p->q_radius > 0.0)) return "q_radius must be > 0";
+  if (p->adjoint != 0 && p->adjoint != 1) return "adjoint must be 0 or 1";
+  if (p->adjoint && p->precision != FVM_F64) return "the adjoint needs precision F64";
   return nullptr;
 }
 
@@ -146,6 +148,16 @@ struct fvm_ctx {
   int* flags;
   double* dt_dev;
   int* lim_dev;
+  // reverse mode (prm.adjoint = 1), double fields of N cells
+  double* aL[5];         // adjoint of the input of the stage after the current one
+  double* aE[5];         // adjoint of the current stage's E (u, v, w, alpha, T)
+  double* ap;            // pressure of the adjoint projection
+  double* apf;           // pressure warm start of the recomputed forward stages
+  double* akap;          // adjoint of the curvature
+  double* aM[3];         // adjoint of the Marangoni vector
+  double* aat;           // adjoint of the smoothed alpha
+  double* atmp;          // between the two smoothing transposes
+  double adj_dt;         // dt of the step being adjoined
   // kernel timing with CUDA events (measurement aid, off by default)
   int prof;
   int prof_n;
@@ -240,6 +252,10 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
   size_t o_flags = pl.take(8 * sizeof(int));
   size_t o_dt = pl.take(2 * sizeof(double));   // dt and 1/dt
   size_t o_lim = pl.take(sizeof(int));
+  constexpr int kAdjFields = 18;
+  size_t o_adj[kAdjFields];
+  if (p.adjoint)
+    for (int q = 0; q < kAdjFields; ++q) o_adj[q] = pl.take(N * sizeof(double));
   if (c) {
     char* w = c->ws;
     for (int q = 0; q < 5; ++q) { c->A[q] = w + o_A[q]; c->B[q] = w + o_B[q]; }
@@ -268,6 +284,21 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
     c->flags = (int*)(w + o_flags);
     c->dt_dev = (double*)(w + o_dt);
     c->lim_dev = (int*)(w + o_lim);
+    if (p.adjoint) {
+      double* a[kAdjFields];
+      for (int q = 0; q < kAdjFields; ++q) a[q] = (double*)(w + o_adj[q]);
+      for (int q = 0; q < 5; ++q) { c->aL[q] = a[q]; c->aE[q] = a[5 + q]; }
+      c->ap = a[10];
+      c->apf = a[11];
+      c->akap = a[12];
+      for (int q = 0; q < 3; ++q) c->aM[q] = a[13 + q];
+      c->aat = a[16];
+      c->atmp = a[17];
+    } else {
+      for (int q = 0; q < 5; ++q) { c->aL[q] = nullptr; c->aE[q] = nullptr; }
+      c->ap = c->apf = c->akap = c->aat = c->atmp = nullptr;
+      for (int q = 0; q < 3; ++q) c->aM[q] = nullptr;
+    }
   }
   return pl.off;
 }
@@ -853,14 +884,213 @@ extern "C" fvm_status fvm_stage_predict(fvm_ctx* ctx, const fvm_state* X, long s
   return predict_impl<double>(ctx, X, step_index, dt, ustar, alpha_out, T_out);
 }
 
-extern "C" {
+// ----- reverse mode of one FP64 step ------------------------------------------
+namespace {
 
-fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index, double dt,
-                            const fvm_state* lam_np1, fvm_state* lam_n, double dtheta[2]) {
-  (void)st_n; (void)step_index; (void)dt; (void)lam_np1; (void)lam_n; (void)dtheta;
-  if (!ctx) return FVM_EINVAL;
-  return set_err(ctx, FVM_EUNSUPPORTED, "the adjoint step is not implemented");
+const double kRK[3][3] = {{0.0, 1.0, 0.0}, {0.75, 0.25, 1.0}, {1.0 / 3.0, 2.0 / 3.0, 0.5}};
+
+double source_x(const fvm_ctx* c, long step_index, int q) {
+  return c->prm.q_x0 + c->prm.q_speed * c->prm.h * ((double)step_index + kRK[q][2]);
 }
+
+// Adjoint of one stage E(X) = (P u*(X), alpha + dt R_alpha(X), T + dt R_T(X)):
+// given aE = dJ/dE, adds (dE/dX)^T aE to lu and dJ/dtheta to scal[8..9].
+// X is the stage input.  kappa, as, tmp, us, b, beta0 and the adjoint
+// buffers serve as scratch; aE is overwritten.
+fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* const* lu,
+                         int* cyc, double* rel) {
+  cudaStream_t s = c->stream;
+  const Geo& g = c->g;
+  const long long N = g.N;
+  // 1. projection: with constant beta, P = I - beta G L^{-1} (-D) is
+  //    symmetric on the interior faces, so lus = P aE_u (wall faces zeroed
+  //    on both sides, as the forward zeroes them)
+  double* aEu[3] = {c->aE[0], c->aE[1], c->aE[2]};
+  double* lus[3] = {(double*)c->us[0], (double*)c->us[1], (double*)c->us[2]};
+  TIMED(c, FVM_K_ADJOINT, 1, launch_zero_wall_faces(g, aEu, s));
+  TIMED(c, FVM_K_DIV_RHS, 1, launch_div_rhs<double>(g, aEu, c->dt_dev, c->b, c->partial, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sum_partials(c->partial, kRedBlocks, c->scal + 3, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sub_mean(c->b, N, c->scal + 3, s));
+  double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};
+  TIMED(c, FVM_K_BETA, 1, launch_beta<double, double>(g, c->ph, X[3], be[0], be[1], be[2], s));
+  TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->ap, N, s));
+  fvm_status st = solve_f64(c, c->ap, c->b, cyc, rel, true);
+  if (st && st != FVM_ENOCONV) return st;
+  fvm_status worst = st;
+  Fields<double> E;
+  for (int d = 0; d < 3; ++d) E.u[d] = aEu[d];
+  E.alpha = c->aE[3];
+  E.T = c->aE[4];
+  Fields<double> Y = E;
+  for (int d = 0; d < 3; ++d) Y.u[d] = lus[d];
+  TIMED(c, FVM_K_CORRECT, 1,
+        launch_correct<double, double>(g, E, Y, aEu, c->ap, be, c->dt_dev, 0.0, 1.0, s));
+  // 2. curvature and smoothed alpha of the stage input
+  double* M[3] = {(double*)c->M[0], (double*)c->M[1], (double*)c->M[2]};
+  const int passes = c->prm.smooth_passes;
+  TIMED(c, FVM_K_INTERFACE, 1, launch_interface<double>(g, c->ph, c->tb, passes, X[3], X[4],
+                                                     (double*)c->kappa, M[0], M[1], M[2], s));
+  const double* at = X[3];
+  if (passes == 1) {
+    TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<double>(g, X[3], (double*)c->as, s));
+    at = (const double*)c->as;
+  } else if (passes == 2) {
+    TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<double>(g, X[3], (double*)c->tmp, s));
+    TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<double>(g, (const double*)c->tmp, (double*)c->as, s));
+    at = (const double*)c->as;
+  }
+  TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->akap, N, s));
+  for (int d = 0; d < 3; ++d) TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->aM[d], N, s));
+  TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->aat, N, s));
+  // 3. transposes of the scalar update, the momentum predictor and the
+  //    interface geometry, then of the smoothing passes
+  AdjArgs A;
+  A.g = g;
+  A.tb = c->tb;
+  for (int q = 0; q < 5; ++q) A.X[q] = X[q];
+  A.kappa = (const double*)c->kappa;
+  A.at = at;
+  for (int d = 0; d < 3; ++d) A.lus[d] = lus[d];
+  A.laE = c->aE[3];
+  A.lTE = c->aE[4];
+  for (int q = 0; q < 5; ++q) A.lu[q] = lu[q];
+  A.lkap = c->akap;
+  for (int d = 0; d < 3; ++d) A.lM[d] = c->aM[d];
+  A.lat = c->aat;
+  A.dth = c->scal + 8;
+  A.dt = c->adj_dt;
+  const Phys& ph = c->ph;
+  A.eps_a = ph.eps_a;
+  A.eps_T = ph.eps_T;
+  A.eps_u = ph.eps_u;
+  A.eps_n = ph.eps_n;
+  for (int q = 0; q < 2; ++q) {
+    A.rho[q] = ph.rho[q];
+    A.mu[q] = ph.mu[q];
+    A.lam[q] = ph.lam[q];
+    A.rcp[q] = ph.rcp[q];
+  }
+  A.sigma0 = ph.sigma0;
+  A.dsdT = ph.dsdT;
+  A.T0 = ph.T0;
+  const double r2 = ph.q_radius * ph.q_radius;
+  A.qunit = r2 > 0.0 ? 2.0 / (M_PI * r2) : 0.0;
+  A.ir2 = r2 > 0.0 ? 1.0 / r2 : 0.0;
+  A.xc = xc;
+  A.yc = ph.q_y0;
+  A.qpower = ph.q_power;
+  for (int d = 0; d < 3; ++d) A.L[d] = ph.L[d];
+  TIMED(c, FVM_K_ADJOINT, 1, launch_adj_scalars(A, s));
+  TIMED(c, FVM_K_ADJOINT, 1, launch_adj_momentum(A, s));
+  TIMED(c, FVM_K_ADJOINT, 1, launch_adj_interface(A, s));
+  if (passes == 0) {
+    TIMED(c, FVM_K_ADJOINT, 1, launch_axpby(N, 1.0, c->aat, 1.0, lu[3], s));
+  } else if (passes == 1) {
+    TIMED(c, FVM_K_ADJOINT, 1, launch_adj_smooth(g, c->aat, lu[3], s));
+  } else {
+    TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->atmp, N, s));
+    TIMED(c, FVM_K_ADJOINT, 1, launch_adj_smooth(g, c->aat, c->atmp, s));
+    TIMED(c, FVM_K_ADJOINT, 1, launch_adj_smooth(g, c->atmp, lu[3], s));
+  }
+  fvm_status e = cuda_check(c, "adjoint stage");
+  return e ? e : worst;
+}
+
+fvm_status step_adjoint_impl(fvm_ctx* c, const fvm_state* st_n, long step_index, double dt,
+                             const fvm_state* lam_np1, fvm_state* lam_n, double* dtheta) {
+  cudaStream_t s = c->stream;
+  const long long N = c->g.N;
+  c->adj_dt = dt;
+  TIMED(c, FVM_K_DT, 1, launch_set_scalar(c->dt_dev, dt, s));
+  // recompute the inputs of stages 2 and 3 (A, B) from st_n
+  cudaError_t ce =
+      cudaMemcpyAsync(c->apf, st_n->p, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (ce != cudaSuccess) return set_err(c, FVM_ECUDA, cudaGetErrorString(ce));
+  void* sp[5] = {st_n->u, st_n->v, st_n->w, st_n->alpha, st_n->T};
+  Fields<double> Sn = fields_of<double>(sp);
+  Fields<double> A = fields_of<double>(c->A);
+  Fields<double> B = fields_of<double>(c->B);
+  int cyc = 0;
+  double rel = 0.0;
+  fvm_status worst = FVM_OK;
+  for (int q = 0; q < 2; ++q) {
+    fvm_status r = stage<double>(c, q == 0 ? Sn : A, Sn, q == 0 ? A : B, c->apf, kRK[q][0],
+                                 kRK[q][1], source_x(c, step_index, q), &cyc, &rel, false);
+    if (r == FVM_ENOCONV) worst = r;
+    else if (r) return r;
+  }
+  const double* Xq[3][5] = {
+      {(const double*)st_n->u, (const double*)st_n->v, (const double*)st_n->w,
+       (const double*)st_n->alpha, (const double*)st_n->T},
+      {(const double*)c->A[0], (const double*)c->A[1], (const double*)c->A[2],
+       (const double*)c->A[3], (const double*)c->A[4]},
+      {(const double*)c->B[0], (const double*)c->B[1], (const double*)c->B[2],
+       (const double*)c->B[3], (const double*)c->B[4]}};
+  double* out[5] = {(double*)lam_n->u, (double*)lam_n->v, (double*)lam_n->w,
+                    (double*)lam_n->alpha, (double*)lam_n->T};
+  const double* lamY[5] = {(const double*)lam_np1->u, (const double*)lam_np1->v,
+                           (const double*)lam_np1->w, (const double*)lam_np1->alpha,
+                           (const double*)lam_np1->T};
+  TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->scal + 8, 2, s));
+  // reverse sweep over Y_q = a_q S_n + b_q E(X_q), X_0 = S_n, X_{q+1} = Y_q:
+  // out accumulates the a_q terms and, last, the stage-1 transpose
+  for (int q = 2; q >= 0; --q) {
+    for (int f = 0; f < 5; ++f) {
+      if (q == 2) {
+        TIMED(c, FVM_K_ADJOINT, 1, launch_axpby(N, kRK[q][0], lamY[f], 0.0, out[f], s));
+      } else if (kRK[q][0] != 0.0) {
+        TIMED(c, FVM_K_ADJOINT, 1, launch_axpby(N, kRK[q][0], lamY[f], 1.0, out[f], s));
+      }
+      TIMED(c, FVM_K_ADJOINT, 1, launch_axpby(N, kRK[q][1], lamY[f], 0.0, c->aE[f], s));
+    }
+    double* const* lu = out;
+    if (q > 0) {
+      for (int f = 0; f < 5; ++f) TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->aL[f], N, s));
+      lu = c->aL;
+    }
+    fvm_status r = adjoint_stage(c, Xq[q], source_x(c, step_index, q), lu, &cyc, &rel);
+    if (r == FVM_ENOCONV) worst = r;
+    else if (r) return r;
+    for (int f = 0; f < 5; ++f) lamY[f] = c->aL[f];
+  }
+  TIMED(c, FVM_K_ADJOINT, 1, launch_zero_wall_faces(c->g, out, s));
+  double th[2];
+  ce = cudaMemcpyAsync(th, c->scal + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return set_err(c, FVM_ECUDA, cudaGetErrorString(ce));
+  dtheta[0] += th[0];
+  dtheta[1] += th[1];
+  fvm_status e = cuda_check(c, "step adjoint");
+  return e ? e : worst;
+}
+
+}  // namespace
+
+extern "C" fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index,
+                                       double dt, const fvm_state* lam_np1, fvm_state* lam_n,
+                                       double dtheta[2]) {
+  if (!ctx) return FVM_EINVAL;
+  if (!st_n || !st_n->u || !st_n->v || !st_n->w || !st_n->alpha || !st_n->T || !st_n->p ||
+      !lam_np1 || !lam_np1->u || !lam_np1->v || !lam_np1->w || !lam_np1->alpha || !lam_np1->T ||
+      !lam_n || !lam_n->u || !lam_n->v || !lam_n->w || !lam_n->alpha || !lam_n->T || !dtheta)
+    return set_err(ctx, FVM_EINVAL, "null pointer");
+  if (!ctx->prm.adjoint) return set_err(ctx, FVM_EINVAL, "context created without adjoint = 1");
+  if (ctx->mixed) return set_err(ctx, FVM_EUNSUPPORTED, "the adjoint is FP64 only");
+  const fvm_params& p = ctx->prm;
+  if (p.rho[0] != p.rho[1] || p.mu[0] != p.mu[1] || p.cp[0] != p.cp[1] ||
+      p.lambda[0] != p.lambda[1])
+    return set_err(ctx, FVM_EUNSUPPORTED, "the adjoint needs equal phase properties");
+  if (!(dt > 0.0)) return set_err(ctx, FVM_EINVAL, "dt must be > 0");
+  const void* a[5] = {lam_np1->u, lam_np1->v, lam_np1->w, lam_np1->alpha, lam_np1->T};
+  const void* b[5] = {lam_n->u, lam_n->v, lam_n->w, lam_n->alpha, lam_n->T};
+  for (int q = 0; q < 5; ++q)
+    for (int r = 0; r < 5; ++r)
+      if (a[q] == b[r]) return set_err(ctx, FVM_EINVAL, "lam_n aliases lam_np1");
+  cudaGetLastError();
+  return step_adjoint_impl(ctx, st_n, step_index, dt, lam_np1, lam_n, dtheta);
+}
+
+extern "C" {
 
 const char* fvm_status_string(fvm_status s) {
   switch (s) {

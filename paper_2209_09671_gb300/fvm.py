@@ -42,6 +42,7 @@ class fvm_params(ctypes.Structure):
         ("coarse_rtol", ctypes.c_double), ("coarse_maxit", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("mx_inner_cycles", ctypes.c_int),
+        ("adjoint", ctypes.c_int),
     ]
 
 
@@ -70,9 +71,10 @@ EXPORTS = ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step", "fvm_p
 KERNEL_CLASSES = ("smooth", "interface", "scalars", "momentum", "div_rhs", "beta", "gs_fine",
                   "gs_coarse", "restrict_fine", "restrict_coarse", "prolong_fine",
                   "prolong_coarse", "coarse_cg", "resnorm", "residual64", "add_correction",
-                  "correct", "dt", "diagnostics", "misc")
+                  "correct", "dt", "diagnostics", "misc", "adjoint")
 
 _lib = None
+FIELDS5 = ("u", "v", "w", "alpha", "T")
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -149,6 +151,7 @@ def make_params(p) -> fvm_params:
     c.coarse_rtol, c.coarse_maxit = float(p.coarse_rtol), int(p.coarse_maxit)
     c.precision = int(p.precision)
     c.mx_inner_cycles = int(p.mx_inner_cycles)
+    c.adjoint = int(getattr(p, "adjoint", 0))
     return c
 
 
@@ -193,14 +196,16 @@ class Solver:
             msg = self.lib.fvm_last_error(self.ctx).decode()
             raise FvmError(st, f"{what}: {msg}")
 
-    def _state(self, s) -> fvm_state:
+    def _state(self, s, need_p=True) -> fvm_state:
         import torch
         st = fvm_state()
-        for k in ("u", "v", "w", "alpha", "T"):
+        for k in FIELDS5:
             t = s[k]
             if not (t.is_cuda and t.dtype == self.rdtype and t.is_contiguous()):
                 raise ValueError(f"field {k} must be a contiguous CUDA {self.rdtype} tensor")
             setattr(st, k, t.data_ptr())
+        if not need_p:
+            return st
         if not (s["p"].is_cuda and s["p"].dtype == torch.float64 and s["p"].is_contiguous()):
             raise ValueError("p must be a contiguous CUDA float64 tensor")
         st.p = s["p"].data_ptr()
@@ -243,14 +248,22 @@ class Solver:
         self._check(rc, "fvm_stage_predict")
         return out
 
-    def fvm_step_adjoint(self, state_n, step_index, dt, lam_np1, lam_n):
-        dth = (ctypes.c_double * 2)()
+    def fvm_step_adjoint(self, state_n, step_index, dt, lam_np1, lam_n=None):
+        """(lam_n, [dJ/d dsigma_dT, dJ/d q_power]) for one FP64 step at dt:
+        lam_n = (dS_{n+1}/dS_n)^T lam_np1.  state_n holds u, v, w, alpha, T, p
+        (read only); lam_np1 and lam_n hold u, v, w, alpha, T (float64 CUDA
+        tensors); lam_n is allocated when None.  The context must have been
+        created with ``adjoint = 1``."""
+        import torch
+        if lam_n is None:
+            lam_n = {k: torch.empty_like(lam_np1[k]) for k in FIELDS5}
+        dth = (ctypes.c_double * 2)(0.0, 0.0)
         rc = self.lib.fvm_step_adjoint(self.ctx, ctypes.byref(self._state(state_n)),
                                        ctypes.c_long(step_index), ctypes.c_double(dt),
-                                       ctypes.byref(self._state(lam_np1)),
-                                       ctypes.byref(self._state(lam_n)), dth)
+                                       ctypes.byref(self._state(lam_np1, need_p=False)),
+                                       ctypes.byref(self._state(lam_n, need_p=False)), dth)
         self._check(rc, "fvm_step_adjoint")
-        return [dth[0], dth[1]]
+        return lam_n, [dth[0], dth[1]]
 
     def fvm_profile(self, on: bool):
         self._check(self.lib.fvm_profile(self.ctx, 1 if on else 0), "fvm_profile")
