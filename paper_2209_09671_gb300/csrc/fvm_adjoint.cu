@@ -16,6 +16,7 @@
 //                    vector (Eq. 2-5 with delta_s = |grad alpha|)
 //   k_adj_smooth     transpose of one [1,2,1]/4 smoothing pass
 // The derivative of |g| at g = 0 is taken as 0.
+#include "fvm_adjoint.h"
 #include "fvm_device.cuh"
 
 namespace fvm {

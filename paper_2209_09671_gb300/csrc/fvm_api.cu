@@ -9,6 +9,7 @@
 
 #include <new>
 
+#include "fvm_adjoint.h"
 #include "fvm_internal.h"
 
 using namespace fvm;

@@ -1,9 +1,9 @@
 // Internal declarations shared by the translation units of libfvm.
 // Host-side launchers are declared here; kernels live in fvm_stage.cu
 // (one forward-Euler stage: smoothing, interface geometry, scalar transport,
-// momentum predictor, projection right-hand side, correction), fvm_mg.cu
-// (geometric multigrid, reductions) and fvm_adjoint.cu (reverse mode of one
-// FP64 stage).
+// momentum predictor, projection right-hand side, correction) and fvm_mg.cu
+// (geometric multigrid, reductions); the reverse-mode kernels are declared in
+// fvm_adjoint.h.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -140,34 +140,5 @@ void launch_residual_norm2(const MGLevel<T>& L, double* partial, double* out, cu
 void launch_residual64(const Geo& g, const double* p, const double* b, float* const* beta,
                        float* r32, double* partial, double* out, cudaStream_t s);
 void launch_add_correction(long long n, double* p, const float* e, cudaStream_t s);
-
-// ----- adjoint stage (fvm_adjoint.cu) -----------------------------------------
-// Arguments of the reverse-mode kernels of one FP64 stage.
-struct AdjArgs {
-  Geo g;
-  TBC tb;
-  const double* X[5];      // stage input u, v, w, alpha, T
-  const double* kappa;     // curvature of the stage input
-  const double* at;        // smoothed alpha of the stage input
-  const double* lus[3];    // adjoint of u*, v*, w*
-  const double* laE;       // adjoint of alpha + dt R_alpha
-  const double* lTE;       // adjoint of T + dt R_T
-  double* lu[5];           // accumulated adjoint of the stage input
-  double* lkap;            // adjoint of kappa
-  double* lM[3];           // adjoint of the Marangoni vector
-  double* lat;             // adjoint of the smoothed alpha
-  double* dth;             // [2]: d/d(dsigma/dT), d/d(q_power)
-  double dt, eps_a, eps_T, eps_u, eps_n;
-  double rho[2], mu[2], lam[2], rcp[2];
-  double sigma0, dsdT, T0;
-  double qunit, ir2, xc, yc, qpower;   // qunit: peak flux per watt, 2/(pi r^2)
-  double L[3];
-};
-void launch_adj_momentum(const AdjArgs& A, cudaStream_t s);
-void launch_adj_scalars(const AdjArgs& A, cudaStream_t s);
-void launch_adj_interface(const AdjArgs& A, cudaStream_t s);
-void launch_adj_smooth(const Geo& g, const double* lout, double* lin, cudaStream_t s);
-void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s);
-void launch_zero_wall_faces(const Geo& g, double* const* u, cudaStream_t s);
 
 }  // namespace fvm
