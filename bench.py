@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--mx-inner", type=int, default=None,
+                    help="float V-cycles per double refinement of the mixed solve (default: the "
+                         "workload's, 2)")
     ap.add_argument("--adjoint", action="store_true",
                     help="instead: the FP64 adjoint workload (gradient of the interface-height "
                          "objective through a checkpointed rollout, and the adjoint step's cost)")
@@ -217,14 +220,14 @@ def run_reference(args, rank, world):
 
 
 def adjoint_workload(n):
-    """The thermocapillary channel physics (equal unit properties, Dirichlet
-    cos(2 pi x/L) bottom wall) at n x n x n with a stationary Gaussian surface
-    source of power 0.5 and a rippled interface, FP64, projections to 1e-11
+    """The thermocapillary channel (equal unit properties, Dirichlet
+    cos(2 pi x/L) bottom wall, flat interface at mid-height) at n x n x n with
+    a stationary Gaussian surface source of power 0.5, FP64, projections to 1e-11
     (about ten times the FP64 rounding floor of the residual of smooth modes
     at 192^3).  The objective is the squared deviation of the column
     interface heights from their initial values, J = sum (H - H0)^2 h^2."""
     import cases
-    p, s = cases.adjoint_channel(nx=n, ny=n, nz=n, q_power=0.5)
+    p, s = cases.adjoint_channel(nx=n, ny=n, nz=n, q_power=0.5, ripple=0.0)
     p = p.replace(precision=cases.F64, mg_rtol=1e-11, mg_max_cycles=200, adjoint=1)
     target = s["alpha"].sum(axis=0) * p.h
     return p, s, target
@@ -311,7 +314,7 @@ def run_adjoint(args, rank, world, local_rank):
         grad = theta.grad.tolist()
         line = {"metric": "adjoint step cost and rollout gradient, FP64",
                 "unit": "ms", "higher_is_better": False, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"thermocapillary channel + Gaussian source "
+                "config": {"workload": f"thermocapillary channel (flat interface) + Gaussian source "
                                        f"{p.nx}x{p.ny}x{p.nz}, FP64, projections to 1e-11",
                            "objective": "sum over columns of (H - H0)^2 h^2",
                            "cells": N, "dt": dt, "rollout_steps": args.adj_steps,
@@ -377,6 +380,8 @@ def run_ours(args, rank, world, local_rank):
 
     # ---------------- mixed-precision step (the headline) -------------------
     p, s0 = make_workload(n, cases.MIXED)
+    if args.mx_inner:
+        p = p.replace(mx_inner_cycles=args.mx_inner)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         solver = P.Solver(p, device=dev, stream=stream)
@@ -531,6 +536,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": f"melt-pool surrogate {n}^3 (rho 7900/1, mixed precision)",
                    "grid": [n, n, n], "precision": "mixed", "mg_rtol": p.mg_rtol,
+                   "mx_inner_cycles": p.mx_inner_cycles,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (state 448 MB)"},
         "roofline": roof,

@@ -260,12 +260,14 @@ def smooth_noise(seed: int, shape, corr_cells: float = 8.0) -> np.ndarray:
 
 
 def adjoint_channel(nx: int = 32, ny: int = 32, nz: int = 16, dT: float = 1.0,
-                    sigmaT: float = 0.01, q_power: float = 0.05):
+                    sigmaT: float = 0.01, q_power: float = 0.05, ripple: float = 0.6):
     """The thermocapillary channel physics (equal unit properties, Dirichlet
     cos(2 pi x / L) bottom wall) with a stationary Gaussian surface source of
-    radius 8 cells at the centre of the interface; the interface carries a
-    small seeded ripple so that curvature, Marangoni and WENO terms are all
-    active.  Used for gradients with respect to theta = (dsigma/dT, q_power)."""
+    radius 8 cells at the centre of the interface; the interface (a tanh
+    profile 1.2 cells wide) carries a seeded ripple of `ripple` cells so that
+    curvature, Marangoni and WENO terms are all active (ripple = 0: the flat
+    interface of the channel).  Used for gradients with respect to
+    theta = (dsigma/dT, q_power)."""
     p, s = thermocapillary_channel(nx=nx, ny=ny, nz=nz, dT=dT, sigmaT=sigmaT)
     h = p.h
     p = p.replace(q_power=q_power, q_radius=8.0 * h, q_x0=0.5 * nx * h, q_y0=0.5 * ny * h,
@@ -273,7 +275,7 @@ def adjoint_channel(nx: int = 32, ny: int = 32, nz: int = 16, dT: float = 1.0,
     x, y, z = cell_centres(p)
     r = uniform(SEED + 7, (4,), 0.0, 1.0)
     Lx, Ly = nx * h, ny * h
-    zi = 0.5 * nz * h + 0.6 * h * (np.cos(2 * math.pi * x / Lx + 6.283 * r[0]) *
+    zi = 0.5 * nz * h + ripple * h * (np.cos(2 * math.pi * x / Lx + 6.283 * r[0]) *
                                     np.cos(2 * math.pi * y / Ly + 6.283 * r[1]))
     s["alpha"][:] = np.broadcast_to(0.5 * (1.0 - np.tanh((z - zi) / (1.2 * h))), p.shape)
     return p, s

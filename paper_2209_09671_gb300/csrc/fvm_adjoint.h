@@ -21,16 +21,19 @@ struct AdjArgs {
   double* lM[3];           // adjoint of the Marangoni vector
   double* lat;             // adjoint of the smoothed alpha
   double* dth;             // [2]: d/d(dsigma/dT), d/d(q_power)
+  double* K;               // kAdjSlots coefficient slots of N doubles each
   double dt, eps_a, eps_T, eps_u, eps_n;
   double rho[2], mu[2], lam[2], rcp[2];
+  double irho;             // 1 / rho (the phases have equal densities)
   double sigma0, dsdT, T0;
   double qunit, ir2, xc, yc, qpower;   // qunit: peak flux per watt, 2/(pi r^2)
   double L[3];
 };
-void launch_adj_momentum(const AdjArgs& A, cudaStream_t s);
-void launch_adj_scalars(const AdjArgs& A, cudaStream_t s);
-void launch_adj_interface(const AdjArgs& A, cudaStream_t s);
-void launch_adj_smooth(const Geo& g, const double* lout, double* lin, cudaStream_t s);
+constexpr int kAdjSlots = 22;
+// each returns the number of kernels it launched
+int launch_adj_momentum(const AdjArgs& A, cudaStream_t s);    // needs lus; adds lkap, lM
+int launch_adj_scalars(const AdjArgs& A, cudaStream_t s);     // needs laE, lTE
+int launch_adj_interface(const AdjArgs& A, cudaStream_t s);   // needs lkap, lM; adds lat
 void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s);
 void launch_zero_wall_faces(const Geo& g, double* const* u, cudaStream_t s);
 

@@ -158,6 +158,7 @@ struct fvm_ctx {
   double* aM[3];         // adjoint of the Marangoni vector
   double* aat;           // adjoint of the smoothed alpha
   double* atmp;          // between the two smoothing transposes
+  double* aK;            // kAdjSlots coefficient slots of the two-pass transposes
   double adj_dt;         // dt of the step being adjoined
   // kernel timing with CUDA events (measurement aid, off by default)
   int prof;
@@ -255,8 +256,11 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
   size_t o_lim = pl.take(sizeof(int));
   constexpr int kAdjFields = 18;
   size_t o_adj[kAdjFields];
-  if (p.adjoint)
+  size_t o_K = 0;
+  if (p.adjoint) {
     for (int q = 0; q < kAdjFields; ++q) o_adj[q] = pl.take(N * sizeof(double));
+    o_K = pl.take((size_t)kAdjSlots * N * sizeof(double));
+  }
   if (c) {
     char* w = c->ws;
     for (int q = 0; q < 5; ++q) { c->A[q] = w + o_A[q]; c->B[q] = w + o_B[q]; }
@@ -295,7 +299,9 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
       for (int q = 0; q < 3; ++q) c->aM[q] = a[13 + q];
       c->aat = a[16];
       c->atmp = a[17];
+      c->aK = (double*)(w + o_K);
     } else {
+      c->aK = nullptr;
       for (int q = 0; q < 5; ++q) { c->aL[q] = nullptr; c->aE[q] = nullptr; }
       c->ap = c->apf = c->akap = c->aat = c->atmp = nullptr;
       for (int q = 0; q < 3; ++q) c->aM[q] = nullptr;
@@ -959,6 +965,7 @@ fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* 
   for (int d = 0; d < 3; ++d) A.lM[d] = c->aM[d];
   A.lat = c->aat;
   A.dth = c->scal + 8;
+  A.K = c->aK;
   A.dt = c->adj_dt;
   const Phys& ph = c->ph;
   A.eps_a = ph.eps_a;
@@ -971,6 +978,7 @@ fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* 
     A.lam[q] = ph.lam[q];
     A.rcp[q] = ph.rcp[q];
   }
+  A.irho = 1.0 / ph.rho[0];
   A.sigma0 = ph.sigma0;
   A.dsdT = ph.dsdT;
   A.T0 = ph.T0;
@@ -981,18 +989,19 @@ fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* 
   A.yc = ph.q_y0;
   A.qpower = ph.q_power;
   for (int d = 0; d < 3; ++d) A.L[d] = ph.L[d];
-  TIMED(c, FVM_K_ADJOINT, 1, launch_adj_scalars(A, s));
-  TIMED(c, FVM_K_ADJOINT, 1, launch_adj_momentum(A, s));
-  TIMED(c, FVM_K_ADJOINT, 1, launch_adj_interface(A, s));
-  if (passes == 0) {
-    TIMED(c, FVM_K_ADJOINT, 1, launch_axpby(N, 1.0, c->aat, 1.0, lu[3], s));
-  } else if (passes == 1) {
-    TIMED(c, FVM_K_ADJOINT, 1, launch_adj_smooth(g, c->aat, lu[3], s));
-  } else {
-    TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->atmp, N, s));
-    TIMED(c, FVM_K_ADJOINT, 1, launch_adj_smooth(g, c->aat, c->atmp, s));
-    TIMED(c, FVM_K_ADJOINT, 1, launch_adj_smooth(g, c->atmp, lu[3], s));
+  TIMED(c, FVM_K_ADJOINT, 8, launch_adj_scalars(A, s));
+  TIMED(c, FVM_K_ADJOINT, 7, launch_adj_momentum(A, s));
+  TIMED(c, FVM_K_ADJOINT, 8, launch_adj_interface(A, s));
+  // the smoothing pass is a symmetric matrix: its transpose is itself
+  const double* lsm = c->aat;
+  if (passes == 1) {
+    TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<double>(g, c->aat, c->atmp, s));
+    lsm = c->atmp;
+  } else if (passes == 2) {
+    TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<double>(g, c->aat, c->atmp, s));
+    TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<double>(g, (const double*)c->atmp, c->aat, s));
   }
+  TIMED(c, FVM_K_ADJOINT, 1, launch_axpby(N, 1.0, lsm, 1.0, lu[3], s));
   fvm_status e = cuda_check(c, "adjoint stage");
   return e ? e : worst;
 }

@@ -344,6 +344,18 @@ void launch_residual_norm2(const MGLevel<T>& L, double* partial, double* out, cu
   launch_sum_partials(partial, kRedBlocks, out, s);
 }
 
+// float -> double for a finite beta >= 0 (normal or zero) with integer
+// operations only: sign and mantissa move over, the exponent is rebiased
+// (127 -> 1023).  GB300 issues FP64 work (conversions included) at a small
+// fraction of the FP32 and integer rates, and this kernel is bound by it.
+__device__ __forceinline__ double beta_to_double(float f) {
+  const unsigned fb = __float_as_uint(f);
+  const unsigned mag = fb & 0x7fffffffu;
+  const unsigned hi = (fb & 0x80000000u) | (((mag >> 23) + 896u) << 20) | ((mag & 0x7fffffu) >> 3);
+  const unsigned lo = fb << 29;
+  return mag == 0u ? 0.0 : __hiloint2double((int)hi, (int)lo);
+}
+
 __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* __restrict__ b,
                              const float* __restrict__ b0, const float* __restrict__ b1,
                              const float* __restrict__ b2, float* __restrict__ r32,
@@ -370,8 +382,8 @@ __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* 
       const int chi = idx[d] == n - 1 ? c - (n - 1) * st[d] : c + st[d];
       const float blo = be[d][c];
       const float bhi = (g.bc[d] == WALL && idx[d] == n - 1) ? 0.f : be[d][chi];
-      lsum = fma((double)blo, pc - p[clo], lsum);
-      lsum = fma((double)bhi, pc - p[chi], lsum);
+      lsum = fma(beta_to_double(blo), pc - p[clo], lsum);
+      lsum = fma(beta_to_double(bhi), pc - p[chi], lsum);
     }
     const double r = fma(-wu, lsum, b[c]);
     r32[c] = (float)r;
