@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 
 FIELDS = A.FIELDS
 # Both sides are FP64 with every projection converged to 1e-13; what remains
-# is the summation order of the scatter-form transposes (atomic adds) against
-# autograd's gather form, a few ulps per term.
+# is the summation order of the two-pass transposes (and of the atomic adds at
+# boundaries) against autograd's, a few ulps per term.
 TOL = 1e-9
 
 
