@@ -328,22 +328,41 @@ def run_adjoint(args, rank, world, local_rank):
                 "backward_over_forward": (t2 - t1) / (t1 - t0),
                 "clocks": clk}
         if args.fd:
-            fd = []
+            # a second, well-conditioned objective on the same rollout:
+            # J_T = sum T^2 h^3 (T changes by O(1), unlike the interface height)
+            def JT_of(T):
+                return (T ** 2).sum() * p.h ** 3
+
+            theta_T = torch.tensor([p.dsigma_dT, p.q_power], dtype=torch.float64, device=dev,
+                                   requires_grad=True)
+            ins_T = {k: state[k].clone().requires_grad_(k != "p") for k in ADJ.STATE_KEYS}
+            out_T = ADJ.Rollout.apply(solver, 0, dts, theta_T,
+                                      *(ins_T[k] for k in P.fvm.FIELDS5), ins_T["p"])
+            JT = JT_of(out_T[4])
+            JT.backward()
+            grad_T = theta_T.grad.tolist()
+            fd, fd_T = [], []
             for q, name in enumerate(("dsigma_dT", "q_power")):
                 v = getattr(p, name)
                 eps = 1e-4 * abs(v)
-                Js = []
+                Js, JTs = [], []
                 for sgn in (1, -1):
                     sv = P.Solver(p.replace(adjoint=0, **{name: v + sgn * eps}), device=dev,
                                   stream=stream)
                     st = {k: x.clone() for k, x in state.items()}
                     ADJ.rollout(sv, st, 0, dts)
                     Js.append(J_of(st["alpha"]).item())
+                    JTs.append(JT_of(st["T"]).item())
                     sv.close()
                     del st
                 fd.append((Js[0] - Js[1]) / (2 * eps))
+                fd_T.append((JTs[0] - JTs[1]) / (2 * eps))
             line["fd"] = {"eps_rel": 1e-4, "dJ_dtheta": fd,
                           "rel_err": [abs(a - b) / abs(b) for a, b in zip(grad, fd)]}
+            line["temperature_objective"] = {
+                "objective": "sum T^2 h^3 after the same rollout", "J": JT.item(),
+                "dJ_dtheta": grad_T, "fd_dJ_dtheta": fd_T,
+                "rel_err": [abs(a - b) / abs(b) for a, b in zip(grad_T, fd_T)]}
     print(json.dumps(line), flush=True)
 
 

@@ -113,7 +113,7 @@ def test_rollout_gradient_matches_central_differences():
         Jp = _rollout_J(P, p.replace(**{name: v + eps}), s, dts, target)
         Jm = _rollout_J(P, p.replace(**{name: v - eps}), s, dts, target)
         fd = (Jp - Jm) / (2 * eps)
-        assert abs(fd - gth[q]) <= 1e-5 * abs(gth[q]), (name, fd, gth[q])
+        assert abs(fd - gth[q]) <= 1e-6 * abs(gth[q]), (name, fd, gth[q])
     # a smooth perturbation of T and u
     z = cases.cell_centres(p)[2]
     delta = {"T": 0.1 * np.cos(2 * np.pi * x / (p.nx * p.h)) * np.sin(np.pi * z),
@@ -124,7 +124,7 @@ def test_rollout_gradient_matches_central_differences():
     Jp = _rollout_J(P, p, s, dts, target, delta, eps)
     Jm = _rollout_J(P, p, s, dts, target, delta, -eps)
     fd = (Jp - Jm) / (2 * eps)
-    assert abs(fd - ad) <= 1e-5 * abs(ad), (fd, ad)
+    assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
     solver.close()
 
 
