@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="cells per axis (default 256)")
+    ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="grid of the melt-pool surrogate (overrides --n), e.g. 512 512 256")
+    ap.add_argument("--mg-levels", type=int, default=None,
+                    help="cap on the multigrid hierarchy depth (default: the workload's)")
     ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
@@ -366,9 +370,11 @@ def run_adjoint(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def make_workload(n, precision):
+def make_workload(shape, precision, mg_levels=None):
     import cases
-    p, s = cases.melt_pool(n, n, n, precision=precision)
+    p, s = cases.melt_pool(*shape, precision=precision)
+    if mg_levels:
+        p = p.replace(mg_levels=mg_levels)
     return p, s
 
 
@@ -383,8 +389,9 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as tdist
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    n = args.n
-    N = n ** 3
+    shape = tuple(args.shape) if args.shape else (args.n,) * 3
+    N = shape[0] * shape[1] * shape[2]
+    grid_name = "x".join(str(v) for v in shape) if len(set(shape)) > 1 else f"{shape[0]}^3"
 
     def barrier():
         if dist:
@@ -398,7 +405,7 @@ def run_ours(args, rank, world, local_rank):
         return t.item()
 
     # ---------------- mixed-precision step (the headline) -------------------
-    p, s0 = make_workload(n, cases.MIXED)
+    p, s0 = make_workload(shape, cases.MIXED, args.mg_levels)
     if args.mx_inner:
         p = p.replace(mx_inner_cycles=args.mx_inner)
     stream = torch.cuda.Stream(device=dev)
@@ -521,7 +528,7 @@ def run_ours(args, rank, world, local_rank):
     # ---------------- FP64 step (side measurement, same workload) ----------
     f64 = None
     if args.f64_steps > 0:
-        p64, s64 = make_workload(n, cases.F64)
+        p64, s64 = make_workload(shape, cases.F64, args.mg_levels)
         with torch.cuda.stream(stream):
             sol64 = P.Solver(p64, device=dev, stream=stream)
             st64 = P.to_device(s64, False, dev)
@@ -553,11 +560,12 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 transport + f64 projection",
         "data": "synthetic",
-        "config": {"workload": f"melt-pool surrogate {n}^3 (rho 7900/1, mixed precision)",
-                   "grid": [n, n, n], "precision": "mixed", "mg_rtol": p.mg_rtol,
+        "config": {"workload": f"melt-pool surrogate {grid_name} (rho 7900/1, mixed precision)",
+                   "grid": list(shape), "precision": "mixed", "mg_rtol": p.mg_rtol,
+                   "mg_levels": p.mg_levels,
                    "mx_inner_cycles": p.mx_inner_cycles,
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (state 448 MB)"},
+                   "l2": f"inputs larger than L2 (state {N * 28 / 2**20:.0f} MiB)"},
         "roofline": roof,
         "roofline_top_hbm_kernel": hbm_top,
         "cpu_baseline": cpu,
