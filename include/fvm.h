@@ -212,7 +212,7 @@ typedef enum {
   FVM_K_BETA, FVM_K_GS_FINE, FVM_K_GS_COARSE, FVM_K_RESTRICT_FINE, FVM_K_RESTRICT_COARSE,
   FVM_K_PROLONG_FINE, FVM_K_PROLONG_COARSE, FVM_K_COARSE_CG, FVM_K_RESNORM,
   FVM_K_RESIDUAL64, FVM_K_ADD_CORRECTION, FVM_K_CORRECT, FVM_K_DT, FVM_K_DIAGNOSTICS,
-  FVM_K_MISC, FVM_K_ADJOINT, FVM_KCLASS_COUNT
+  FVM_K_MISC, FVM_K_ADJOINT, FVM_K_COARSE_TAIL, FVM_KCLASS_COUNT
 } fvm_kernel_class;
 
 fvm_status fvm_profile(fvm_ctx* ctx, int on);

@@ -375,11 +375,37 @@ void smooth(fvm_ctx* c, MGLevel<T>& L, int l, int iters, int first) {
   }
 }
 
+// first level of the one-CTA coarse tail (at most kTailCells cells, not the
+// finest, at least one level above the coarsest), or -1
+int tail_start(const fvm_ctx* c) {
+  for (int l = 1; l < c->nlev - 1; ++l) {
+    const LevelShape& q = c->shp[l];
+    if ((long long)q.n[0] * q.n[1] * q.n[2] <= kTailCells)
+      return c->nlev - l <= kTailLevels ? l : -1;
+  }
+  return -1;
+}
+
 // V(pre, post) cycle: red-black sweeps before the coarse correction,
-// black-red after, CG on the coarsest level
+// black-red after, CG on the coarsest level; the levels from tail_start()
+// down run in one kernel
 template <typename T>
 void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
   cudaStream_t s = c->stream;
+  if (l == tail_start(c)) {
+    TailArgs<T> A;
+    A.nl = c->nlev - l;
+    for (int q = 0; q < A.nl; ++q) A.L[q] = Ls[l + q];
+    A.r = (double*)c->cg[0];
+    A.d = (double*)c->cg[1];
+    A.Ad = (double*)c->cg[2];
+    A.rtol = coarse_rtol;
+    A.maxit = c->prm.coarse_maxit;
+    A.pre = c->prm.mg_pre;
+    A.post = c->prm.mg_post;
+    TIMED(c, FVM_K_COARSE_TAIL, 1, launch_coarse_tail<T>(A, s));
+    return;
+  }
   if (l == c->nlev - 1) {
     TIMED(c, FVM_K_COARSE_CG, 1, launch_coarse_cg<T>(Ls[l], (double*)c->cg[0], (double*)c->cg[1], (double*)c->cg[2],
                                                    coarse_rtol, c->prm.coarse_maxit, s));

@@ -129,6 +129,20 @@ template <typename T>
 void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
 template <typename T>
 void launch_beta_coarsen(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
+// The coarse tail of a V-cycle (levels of at most kTailCells cells, the
+// coarsest solved by CG) in one CTA
+constexpr int kTailCells = 4096;
+constexpr int kTailLevels = 8;
+template <typename T>
+struct TailArgs {
+  int nl;                      // levels in the tail, the last one the coarsest
+  MGLevel<T> L[kTailLevels];
+  double *r, *d, *Ad;          // CG vectors (as launch_coarse_cg)
+  double rtol;
+  int maxit, pre, post;
+};
+template <typename T>
+void launch_coarse_tail(const TailArgs<T>& A, cudaStream_t s);
 // CG vectors are double in both precisions (the coarsest level is small)
 template <typename T>
 void launch_coarse_cg(const MGLevel<T>& L, double* r, double* d, double* Ad, double rtol,

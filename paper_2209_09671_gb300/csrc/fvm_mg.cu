@@ -150,15 +150,10 @@ __device__ __forceinline__ void decode_lv(const Geo& g, long long c, int& i, int
 }
 
 // ---------------------------------------------------------------------------
+// Gauss-Seidel update of one cell (its colour's neighbours are fixed)
 template <typename T>
-__global__ void k_gs(MGLevel<T> L, int colour) {
+__device__ __forceinline__ void gs_point(const MGLevel<T>& L, int i, int j, int k) {
   const Geo& g = L.geo;
-  const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z * blockDim.z + threadIdx.z;
-  if (j >= g.n[1] || k >= g.n[2]) return;
-  const int i = 2 * i2 + ((colour + j + k) & 1);
-  if (i >= g.n[0]) return;
   const int c = (k * g.n[1] + j) * g.n[0] + i;
   OpNb<T> nb;
   neighbours(L, i, j, k, c, nb);
@@ -175,6 +170,18 @@ __global__ void k_gs(MGLevel<T> L, int colour) {
 }
 
 template <typename T>
+__global__ void k_gs(MGLevel<T> L, int colour) {
+  const Geo& g = L.geo;
+  const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (j >= g.n[1] || k >= g.n[2]) return;
+  const int i = 2 * i2 + ((colour + j + k) & 1);
+  if (i >= g.n[0]) return;
+  gs_point(L, i, j, k);
+}
+
+template <typename T>
 void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s) {
   const int hx = (L.geo.n[0] + 1) / 2;
   dim3 bs(32, 4, 2);
@@ -184,9 +191,8 @@ void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s) {
 
 // coarse b = mean over children of (b - L x) on the fine level; coarse x = 0
 template <typename T>
-__global__ void k_residual_restrict(MGLevel<T> F, MGLevel<T> C) {
-  long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (cc >= C.geo.N) return;
+__device__ __forceinline__ void restrict_point(const MGLevel<T>& F, const MGLevel<T>& C,
+                                               long long cc) {
   int I, J, K;
   decode_lv(C.geo, cc, I, J, K);
   T acc = T(0);
@@ -206,18 +212,31 @@ __global__ void k_residual_restrict(MGLevel<T> F, MGLevel<T> C) {
 }
 
 template <typename T>
+__global__ void k_residual_restrict(MGLevel<T> F, MGLevel<T> C) {
+  long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (cc >= C.geo.N) return;
+  restrict_point(F, C, cc);
+}
+
+template <typename T>
 void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s) {
   k_residual_restrict<T><<<grid1d(C.geo.N, 128), 128, 0, s>>>(F, C);
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_point(const MGLevel<T>& F, const MGLevel<T>& C,
+                                              long long c) {
+  int i, j, k;
+  decode_lv(F.geo, c, i, j, k);
+  long long p = lin(C.geo, i / F.f[0], j / F.f[1], k / F.f[2]);
+  F.x[c] = F.x[c] + C.x[p];
 }
 
 template <typename T>
 __global__ void k_prolong(MGLevel<T> F, MGLevel<T> C) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.geo.N) return;
-  int i, j, k;
-  decode_lv(F.geo, c, i, j, k);
-  long long p = lin(C.geo, i / F.f[0], j / F.f[1], k / F.f[2]);
-  F.x[c] = F.x[c] + C.x[p];
+  prolong_point(F, C, c);
 }
 
 template <typename T>
@@ -255,11 +274,9 @@ void launch_beta_coarsen(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t 
 // x0 = 0, stop at ||r|| <= rtol ||b|| or on breakdown, mean-free result.
 // The vectors are double in both precisions.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, double* __restrict__ r,
-                                                    double* __restrict__ dd,
-                                                    double* __restrict__ Ad, double rtol,
-                                                    int maxit) {
-  __shared__ double sh[33];
+__device__ void coarse_cg_block(const MGLevel<T>& L, double* __restrict__ r,
+                                double* __restrict__ dd, double* __restrict__ Ad, double rtol,
+                                int maxit, double* sh) {
   const Geo& g = L.geo;
   const int N = (int)g.N;
   double acc = 0.0;
@@ -312,6 +329,66 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, double* __rest
   for (int c = threadIdx.x; c < N; c += blockDim.x) acc += x[c];
   double xm = block_sum_all(acc, sh) / (double)N;
   for (int c = threadIdx.x; c < N; c += blockDim.x) L.x[c] = (T)(x[c] - xm);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, double* __restrict__ r,
+                                                    double* __restrict__ dd,
+                                                    double* __restrict__ Ad, double rtol,
+                                                    int maxit) {
+  __shared__ double sh[33];
+  coarse_cg_block(L, r, dd, Ad, rtol, maxit, sh);
+}
+
+// The coarse tail of a V-cycle in one CTA: levels small enough that a kernel
+// launch per sweep costs more than the sweep.  The same point updates as the
+// per-level kernels, in the same order of phases (pre-sweeps red first,
+// residual restriction, ..., CG on the coarsest level, ..., prolongation,
+// post-sweeps black first), separated by block barriers; within one colour
+// sweep (and within restriction and prolongation) the points are
+// independent, so the result equals that of the per-level kernels bit for bit.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A) {
+  __shared__ double sh[33];
+  const int last = A.nl - 1;
+  for (int l = 0; l < last; ++l) {
+    const MGLevel<T>& L = A.L[l];
+    const Geo& g = L.geo;
+    for (int it = 0; it < A.pre; ++it)
+      for (int col = 0; col < 2; ++col) {
+        for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) {
+          int i, j, k;
+          decode_lv(g, c, i, j, k);
+          if (((i + j + k) & 1) == col) gs_point(L, i, j, k);
+        }
+        __syncthreads();
+      }
+    for (int cc = threadIdx.x; cc < (int)A.L[l + 1].geo.N; cc += blockDim.x)
+      restrict_point(L, A.L[l + 1], cc);
+    __syncthreads();
+  }
+  coarse_cg_block(A.L[last], A.r, A.d, A.Ad, A.rtol, A.maxit, sh);
+  __syncthreads();
+  for (int l = last - 1; l >= 0; --l) {
+    const MGLevel<T>& L = A.L[l];
+    const Geo& g = L.geo;
+    for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) prolong_point(L, A.L[l + 1], c);
+    __syncthreads();
+    for (int it = 0; it < A.post; ++it)
+      for (int col = 0; col < 2; ++col) {
+        for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) {
+          int i, j, k;
+          decode_lv(g, c, i, j, k);
+          if (((i + j + k) & 1) == 1 - col) gs_point(L, i, j, k);
+        }
+        __syncthreads();
+      }
+  }
+}
+
+template <typename T>
+void launch_coarse_tail(const TailArgs<T>& A, cudaStream_t s) {
+  k_coarse_tail<T><<<1, 1024, 0, s>>>(A);
 }
 
 template <typename T>
@@ -417,6 +494,7 @@ void launch_add_correction(long long n, double* p, const float* e, cudaStream_t 
                                             cudaStream_t);                                   \
   template void launch_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);       \
   template void launch_beta_coarsen<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);  \
+  template void launch_coarse_tail<T>(const TailArgs<T>&, cudaStream_t);                     \
   template void launch_coarse_cg<T>(const MGLevel<T>&, double*, double*, double*, double,  \
                                     int, cudaStream_t);                                      \
   template void launch_residual_norm2<T>(const MGLevel<T>&, double*, double*, cudaStream_t);

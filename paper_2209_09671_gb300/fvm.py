@@ -71,7 +71,7 @@ EXPORTS = ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step", "fvm_p
 KERNEL_CLASSES = ("smooth", "interface", "scalars", "momentum", "div_rhs", "beta", "gs_fine",
                   "gs_coarse", "restrict_fine", "restrict_coarse", "prolong_fine",
                   "prolong_coarse", "coarse_cg", "resnorm", "residual64", "add_correction",
-                  "correct", "dt", "diagnostics", "misc", "adjoint")
+                  "correct", "dt", "diagnostics", "misc", "adjoint", "coarse_tail")
 
 _lib = None
 FIELDS5 = ("u", "v", "w", "alpha", "T")
