@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="cells per axis (default 256)")
     ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
                     help="grid of the melt-pool surrogate (overrides --n), e.g. 512 512 256")
+    ap.add_argument("--mg-pre", type=int, default=None, help="pre-smoothing sweeps (default 2)")
+    ap.add_argument("--mg-post", type=int, default=None, help="post-smoothing sweeps (default 2)")
     ap.add_argument("--mg-levels", type=int, default=None,
                     help="cap on the multigrid hierarchy depth (default: the workload's)")
     ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
@@ -408,6 +410,10 @@ def run_ours(args, rank, world, local_rank):
     p, s0 = make_workload(shape, cases.MIXED, args.mg_levels)
     if args.mx_inner:
         p = p.replace(mx_inner_cycles=args.mx_inner)
+    if args.mg_pre is not None:
+        p = p.replace(mg_pre=args.mg_pre)
+    if args.mg_post is not None:
+        p = p.replace(mg_post=args.mg_post)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         solver = P.Solver(p, device=dev, stream=stream)
@@ -563,7 +569,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": f"melt-pool surrogate {grid_name} (rho 7900/1, mixed precision)",
                    "grid": list(shape), "precision": "mixed", "mg_rtol": p.mg_rtol,
                    "mg_levels": p.mg_levels,
-                   "mx_inner_cycles": p.mx_inner_cycles,
+                   "mx_inner_cycles": p.mx_inner_cycles, "mg_pre": p.mg_pre,
+                   "mg_post": p.mg_post,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": f"inputs larger than L2 (state {N * 28 / 2**20:.0f} MiB)"},
         "roofline": roof,
