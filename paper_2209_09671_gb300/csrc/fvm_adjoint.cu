@@ -188,24 +188,19 @@ __device__ double weno5_grad(const double* v, double eps, double* gr) {
 }
 
 // flux U * WENO5 (upwind by the sign of U) from v[0..5] (offsets -3..2 of the
-// face): *dU = dF/dU, gv[m] = dF/dv[m]
+// face): *dU = dF/dU, gv[m] = dF/dv[m].  The upwind stencil is selected
+// before one reconstruction (one inlined copy of the derivative code: the
+// kernels that call this several times are bound by instruction fetch).
 __device__ void upwind_grad(double U, const double* v, double eps, double* dU, double* gv) {
-  double g5[5];
+  const bool pos = U >= 0.0;
+  double in[5], g5[5];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) gv[m] = 0.0;
-  double w;
-  if (U >= 0.0) {
-    const double in[5] = {v[0], v[1], v[2], v[3], v[4]};
-    w = weno5_grad(in, eps, g5);
+  for (int m = 0; m < 5; ++m) in[m] = pos ? v[m] : v[5 - m];
+  *dU = weno5_grad(in, eps, g5);
+  gv[0] = pos ? U * g5[0] : 0.0;
+  gv[5] = pos ? 0.0 : U * g5[0];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) gv[m] = U * g5[m];
-  } else {
-    const double in[5] = {v[5], v[4], v[3], v[2], v[1]};
-    w = weno5_grad(in, eps, g5);
-#pragma unroll
-    for (int m = 0; m < 5; ++m) gv[5 - m] = U * g5[m];
-  }
-  *dU = w;
+  for (int m = 1; m < 5; ++m) gv[m] = U * (pos ? g5[m] : g5[5 - m]);
 }
 
 __device__ __forceinline__ double warp_sum_a(double v) {
