@@ -380,15 +380,39 @@ def make_workload(shape, precision, mg_levels=None):
     return p, s
 
 
+def ranks_barrier():
+    """Barrier over the ranks of the default process group (none: no-op)."""
+    import torch.distributed as tdist
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
+        tdist.barrier()
+
+
+def max_over_ranks(x: float, device) -> float:
+    """Max of x over the ranks of the default process group (x itself when
+    there is none); device is where the reduction tensor lives (CUDA for
+    NCCL, CPU for gloo)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(cells_per_rank: int, world: int, seconds: float) -> float:
+    """Cell-updates per second of the whole job: every rank runs an
+    independent replica of the same workload, and the job takes as long as
+    its slowest rank (seconds = the max over ranks)."""
+    return world * cells_per_rank / seconds
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
     import cases
     import paper_2209_09671_gb300 as P
 
-    dist = world > 1
-    if dist:
-        import torch.distributed as tdist
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     shape = tuple(args.shape) if args.shape else (args.n,) * 3
@@ -396,15 +420,7 @@ def run_ours(args, rank, world, local_rank):
     grid_name = "x".join(str(v) for v in shape) if len(set(shape)) > 1 else f"{shape[0]}^3"
 
     def barrier():
-        if dist:
-            tdist.barrier()
-
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return t.item()
+        ranks_barrier()
 
     # ---------------- mixed-precision step (the headline) -------------------
     p, s0 = make_workload(shape, cases.MIXED, args.mg_levels)
@@ -456,8 +472,8 @@ def run_ours(args, rank, world, local_rank):
     solver.fvm_profile(False)
     info = solver.fvm_step(state, step_idx, 0.0, info=True)   # untimed: state sanity
     step_idx += 1
-    t_step = max_over_ranks(elapsed / args.steps)
-    value = world * N / t_step
+    t_step = max_over_ranks(elapsed / args.steps, dev)
+    value = whole_job_rate(N, world, t_step)
 
     # dominant kernel and its roofline
     peak, peak_kind = load_peaks()
@@ -524,8 +540,8 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         stream.synchronize()
         barrier()
-        e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3 / e2e_steps)
-        e2e = {"value": world * N / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e_t = max_over_ranks(e0.elapsed_time(e1) / 1e3 / e2e_steps, dev)
+        e2e = {"value": whole_job_rate(N, world, e2e_t), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
     solver.close()
     del state, solver
@@ -547,10 +563,10 @@ def run_ours(args, rank, world, local_rank):
             sol64.fvm_step(st64, 1 + q, 0.0, info=False)
         a1.record(stream)
         stream.synchronize()
-        t64 = max_over_ranks(a0.elapsed_time(a1) / 1e3 / args.f64_steps)
+        t64 = max_over_ranks(a0.elapsed_time(a1) / 1e3 / args.f64_steps, dev)
         prof64 = sol64.fvm_profile_read()
         inf64 = sol64.fvm_step(st64, 1 + args.f64_steps, 0.0, info=True)
-        f64 = {"value": world * N / t64, "ms_per_step": t64 * 1e3, "steps": args.f64_steps,
+        f64 = {"value": whole_job_rate(N, world, t64), "ms_per_step": t64 * 1e3, "steps": args.f64_steps,
                "vcycles_last_step": inf64["vcycles"],
                "kernels_ms": {k: round(v[1], 2) for k, v in prof64.items() if v[0]},
                "bound": "alu (FP64 units)"}
