@@ -633,7 +633,7 @@ __device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>&
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 1)
     k_momentum(Geo g, PhysR<R> ph, TBC tb, Fields<R> X, const R* __restrict__ kappa,
                const R* __restrict__ M0, const R* __restrict__ M1, const R* __restrict__ M2,
                R* __restrict__ us0, R* __restrict__ us1, R* __restrict__ us2,
@@ -660,6 +660,9 @@ void launch_momentum(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, c
                      const double* dt, cudaStream_t s) {
   const int smem = (int)sizeof(MomShared<R>);
   cudaFuncSetAttribute(k_momentum<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // float tiles (71 KB) fit three CTAs per SM when the L1/shared split favours shared memory
+  cudaFuncSetAttribute(k_momentum<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   k_momentum<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
       g, make_physr<R>(ph, g), tb, X, kappa, M0, M1, M2, us0, us1, us2, dt);
 }
