@@ -279,7 +279,7 @@ __device__ __forceinline__ R face_normal(const R* __restrict__ s2, int lx, int l
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     k_interface(Geo g, PhysR<R> ph, TBC tb, int passes, const R* __restrict__ alpha,
                 const R* __restrict__ T, R* __restrict__ kappa, R* __restrict__ M0,
                 R* __restrict__ M1, R* __restrict__ M2) {
@@ -347,6 +347,8 @@ void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, int passes, c
                       const R* T, R* kappa, R* M0, R* M1, R* M2, cudaStream_t s) {
   const int smem = (int)sizeof(IfaceShared<R>);
   cudaFuncSetAttribute(k_interface<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_interface<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   k_interface<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
       g, make_physr<R>(ph, g), tb, passes, alpha, T, kappa, M0, M1, M2);
 }
@@ -390,7 +392,7 @@ __device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     k_scalars(Geo g, PhysR<R> ph, TBC tb, Fields<R> X, Fields<R> Sn, Fields<R> Y,
               const double* __restrict__ dtp, R a, R b, R xc, R yc, R qamp, R ir2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -466,6 +468,8 @@ void launch_scalars(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, Fi
   double ir2 = ph.q_power != 0.0 ? 1.0 / r2 : 0.0;
   const int smem = (int)sizeof(ScalShared<R>);
   cudaFuncSetAttribute(k_scalars<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_scalars<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   k_scalars<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
       g, make_physr<R>(ph, g), tb, X, Sn, Y, dt, (R)a, (R)b, (R)xc, (R)ph.q_y0, (R)qamp, (R)ir2);
 }
