@@ -11,7 +11,6 @@ Full-size checks use what the oracle can compute piece by piece:
 * properties that hold at any size: the projection residual, conservation
   of sum(alpha), finiteness.
 """
-import math
 
 import numpy as np
 import pytest

@@ -1,7 +1,6 @@
 """GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
 the same seeded inputs.  F64 bar: relative L2 <= 1e-11 per field per step
 with the same number of multigrid cycles on both sides."""
-import math
 
 import numpy as np
 import pytest

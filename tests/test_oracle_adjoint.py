@@ -1,7 +1,6 @@
 """Pins of the oracle's reverse mode (the reference for the GPU adjoint step):
 central finite differences of the oracle step along random state directions
 and in each parameter theta = (dsigma/dT, q_power)."""
-import numpy as np
 import torch
 
 import cases

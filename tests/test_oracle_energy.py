@@ -1,10 +1,8 @@
 """Pins of the temperature equation (advection-diffusion with the surface
 heat flux): exact linear conduction between Dirichlet walls and the energy
 deposited by the Gaussian flux through a flat interface."""
-import math
 
 import numpy as np
-import torch
 
 import cases
 from oracle import fvm_oracle as O
