@@ -189,12 +189,14 @@ fvm_status fvm_stage_predict(fvm_ctx* ctx, const fvm_state* X, long step_index, 
  * into (the caller zeroes them).  The stages are recomputed from st_n; the
  * three projections are adjoined by the same multigrid solve (the operator
  * is symmetric for constant beta).  Requirements, else an error and no
- * write: a context created with adjoint = 1 and precision F64 (EINVAL /
- * EUNSUPPORTED), equal rho, mu, cp and lambda in both phases
+ * write: a context created with adjoint = 1 (EINVAL; fvm_create accepts
+ * adjoint = 1 only with precision F64, and the workspace then holds 40 more
+ * double fields of N cells), equal rho, mu, cp and lambda in both phases
  * (EUNSUPPORTED: the projection coefficient and the transport coefficients
- * are then constant), dt > 0 (EINVAL).  The derivative of |g| at g = 0 is
- * taken as 0.  Entries of lam_n on wall faces are 0.  Synchronises the
- * context's stream. */
+ * are then constant), dt > 0 (EINVAL).  A projection that stops at
+ * mg_max_cycles above mg_rtol returns FVM_ENOCONV after completing the
+ * sweep.  The derivative of |g| at g = 0 is taken as 0.  Entries of lam_n on
+ * wall faces are 0.  Synchronises the context's stream. */
 fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long step_index,
                             double dt, const fvm_state* lam_np1, fvm_state* lam_n,
                             double dtheta[2]);
