@@ -191,10 +191,9 @@ void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s) {
 
 // coarse b = mean over children of (b - L x) on the fine level; coarse x = 0
 template <typename T>
-__device__ __forceinline__ void restrict_point(const MGLevel<T>& F, const MGLevel<T>& C,
-                                               long long cc) {
-  int I, J, K;
-  decode_lv(C.geo, cc, I, J, K);
+__device__ __forceinline__ void restrict_point(const MGLevel<T>& F, const MGLevel<T>& C, int I,
+                                               int J, int K) {
+  const long long cc = lin(C.geo, I, J, K);
   T acc = T(0);
   int cnt = 0;
   for (int dz = 0; dz < F.f[2]; ++dz)
@@ -212,15 +211,40 @@ __device__ __forceinline__ void restrict_point(const MGLevel<T>& F, const MGLeve
 }
 
 template <typename T>
+__device__ __forceinline__ void restrict_point(const MGLevel<T>& F, const MGLevel<T>& C,
+                                               long long cc) {
+  int I, J, K;
+  decode_lv(C.geo, cc, I, J, K);
+  restrict_point(F, C, I, J, K);
+}
+
+// one thread per coarse cell on a 3D grid (no index division per thread)
+template <typename T>
 __global__ void k_residual_restrict(MGLevel<T> F, MGLevel<T> C) {
-  long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (cc >= C.geo.N) return;
-  restrict_point(F, C, cc);
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z * blockDim.z + threadIdx.z;
+  if (I >= C.geo.n[0] || J >= C.geo.n[1] || K >= C.geo.n[2]) return;
+  restrict_point(F, C, I, J, K);
 }
 
 template <typename T>
 void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s) {
-  k_residual_restrict<T><<<grid1d(C.geo.N, 128), 128, 0, s>>>(F, C);
+  const dim3 bs(32, 4, 2);
+  const dim3 gs((C.geo.n[0] + 31) / 32, (C.geo.n[1] + 3) / 4, (C.geo.n[2] + 1) / 2);
+  k_residual_restrict<T><<<gs, bs, 0, s>>>(F, C);
+}
+
+// the coarsening factor of an axis is 1 or 2
+__device__ __forceinline__ int coarse_index(int i, int f) { return f == 2 ? (i >> 1) : i; }
+
+template <typename T>
+__device__ __forceinline__ void prolong_point(const MGLevel<T>& F, const MGLevel<T>& C, int i,
+                                              int j, int k) {
+  const long long c = lin(F.geo, i, j, k);
+  const long long p = lin(C.geo, coarse_index(i, F.f[0]), coarse_index(j, F.f[1]),
+                          coarse_index(k, F.f[2]));
+  F.x[c] = F.x[c] + C.x[p];
 }
 
 template <typename T>
@@ -228,20 +252,24 @@ __device__ __forceinline__ void prolong_point(const MGLevel<T>& F, const MGLevel
                                               long long c) {
   int i, j, k;
   decode_lv(F.geo, c, i, j, k);
-  long long p = lin(C.geo, i / F.f[0], j / F.f[1], k / F.f[2]);
-  F.x[c] = F.x[c] + C.x[p];
+  prolong_point(F, C, i, j, k);
 }
 
+// one thread per fine cell on a 3D grid (no index division per thread)
 template <typename T>
 __global__ void k_prolong(MGLevel<T> F, MGLevel<T> C) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= F.geo.N) return;
-  prolong_point(F, C, c);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (i >= F.geo.n[0] || j >= F.geo.n[1] || k >= F.geo.n[2]) return;
+  prolong_point(F, C, i, j, k);
 }
 
 template <typename T>
 void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s) {
-  k_prolong<T><<<grid1d(F.geo.N, 256), 256, 0, s>>>(F, C);
+  const dim3 bs(32, 4, 2);
+  const dim3 gs((F.geo.n[0] + 31) / 32, (F.geo.n[1] + 3) / 4, (F.geo.n[2] + 1) / 2);
+  k_prolong<T><<<gs, bs, 0, s>>>(F, C);
 }
 
 template <typename T>
