@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--adj-n", type=int, default=192, help="adjoint workload: cells per axis")
     ap.add_argument("--adj-steps", type=int, default=200, help="adjoint workload: rollout steps")
     ap.add_argument("--adj-every", type=int, default=20, help="adjoint workload: checkpoint interval")
+    ap.add_argument("--droplet", action="store_true",
+                    help="instead: the migrating droplet of the paper's Sec. V-A at 100 x 100, FP64, "
+                         "to t = 0.12 s (validation run, one JSON line)")
     ap.add_argument("--fd", action="store_true",
                     help="adjoint workload: also central differences in theta (4 more rollouts)")
     return ap.parse_args()
@@ -371,6 +374,62 @@ def run_adjoint(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_droplet(args, rank, world, local_rank):
+    """The migrating droplet (Table 1) at 100 x 100 in FP64 from rest to
+    t = 0.12 s with dt from the stability limits: steps, GPU time, the
+    droplet's centroid displacement and migration speed, the largest
+    velocity, the change of the phase volume and the mirror asymmetry."""
+    import numpy as np
+    import torch
+
+    import cases
+    import paper_2209_09671_gb300 as P
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p, s0 = cases.ma_bothe_droplet(n=100)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        solver = P.Solver(p, device=dev, stream=stream)
+        st = P.to_device(s0, False, dev)
+    _, y, _ = cases.cell_centres(p)
+    yy = torch.tensor(np.broadcast_to(y, p.shape).copy(), device=dev)
+
+    def centroid():
+        return ((st["alpha"] * yy).sum() / st["alpha"].sum()).item()
+
+    vol0 = st["alpha"].sum().item()
+    y0 = centroid()
+    t, n, hist = 0.0, 0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    while t < 0.12:
+        info = solver.fvm_step(st, n, 0.0, info=True)
+        t += info["dt"]
+        n += 1
+        if n % 500 == 0:
+            hist.append((t, centroid()))
+    e1.record(stream)
+    stream.synchronize()
+    hist.append((t, centroid()))
+    a = st["alpha"]
+    u, v = st["u"], st["v"]
+    t1, c1 = hist[-1]
+    tm, cm = min(hist, key=lambda q: abs(q[0] - 0.9 * t1))
+    line = {"metric": "migrating droplet (Sec. V-A) at 100x100, FP64, to t = 0.12 s",
+            "unit": "s", "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Ma-Bothe droplet, Table 1 properties, 200 K/m, 100x100x1"},
+            "steps": n, "t_end": t, "gpu_seconds": e0.elapsed_time(e1) / 1e3,
+            "centroid_shift_m": c1 - y0, "centroid_shift_cells": (c1 - y0) / p.h,
+            "migration_speed_end_m_per_s": (c1 - cm) / (t1 - tm) if t1 > tm else None,
+            "max_speed_m_per_s": max(u.abs().max().item(), v.abs().max().item()),
+            "volume_change_rel": abs(a.sum().item() - vol0) / vol0,
+            "mirror_asymmetry_alpha": (a - a.flip(-1)).abs().max().item(),
+            "centroid_history": hist}
+    print(json.dumps(line), flush=True)
+
+
 def make_workload(shape, precision, mg_levels=None):
     import cases
     p, s = cases.melt_pool(*shape, precision=precision)
@@ -611,6 +670,9 @@ def main():
         return
     if args.adjoint:
         run_adjoint(args, rank, world, local_rank)
+        return
+    if args.droplet:
+        run_droplet(args, rank, world, local_rank)
         return
     if world > 1:
         import torch

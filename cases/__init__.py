@@ -190,6 +190,38 @@ def static_drop(n: int = 64, seed: int = SEED, subsamples: int = 16):
     return p, s
 
 
+def ma_bothe_droplet(n: int = 100, precision: int = F64, subsamples: int = 8):
+    """The migrating droplet of Sec. V-A (Table 1): a 2D box of 4a x 4a,
+    a = 1.44e-3 m, on n x n x 1 cells; a droplet of radius a (alpha = 1) at
+    the centre in a medium (alpha = 0) with rho 250 / 500, c_p 5e-5 / 1e-4,
+    mu 0.012 / 0.024, lambda 1.2e-6 / 2.4e-6 (medium / droplet), sigma = 0.1
+    and Marangoni coefficient 0.02, read as sigma = 0.1 - 0.02 (T - 290).
+    No-slip walls, Neumann temperature on the side walls and Dirichlet on the
+    bottom (290 K) and top (290 + 200 K/m * 4a), the initial temperature the
+    linear profile between them, the fluid at rest, no gravity.  alpha is the
+    cell area fraction from subsamples^2 points per cell."""
+    a = 1.44e-3
+    L = 4.0 * a
+    h = L / n
+    grad = 200.0
+    p = Params(nx=n, ny=n, nz=1, h=h, bc=(WALL, WALL, PERIODIC),
+               tbc=(NEUMANN, NEUMANN, DIRICHLET, DIRICHLET, NEUMANN, NEUMANN),
+               tbc_T0=(0.0, 0.0, 290.0, 290.0 + grad * L, 0.0, 0.0),
+               tbc_dTamp=(0.0,) * 6,
+               rho=(250.0, 500.0), mu=(0.012, 0.024), cp=(5e-5, 1e-4), lam=(1.2e-6, 2.4e-6),
+               sigma0=0.1, dsigma_dT=-0.02, T0=290.0, g=(0.0, 0.0, 0.0),
+               weno_scale=(1.0, grad * L, 0.01), precision=precision)
+    sub = (np.arange(subsamples) + 0.5) / subsamples
+    xs = ((np.arange(n)[:, None] + sub[None, :]) * h).reshape(-1)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")                        # [y, x]
+    inside = (np.hypot(X - 0.5 * L, Y - 0.5 * L) < a).astype(np.float64)
+    s = zero_state(p)
+    s["alpha"][0] = inside.reshape(n, subsamples, n, subsamples).mean(axis=(1, 3))
+    _, y, _ = cell_centres(p)
+    s["T"][:] = np.broadcast_to(290.0 + grad * y, p.shape)
+    return p, s
+
+
 def thermocapillary_channel(nx: int = 128, ny: int = 128, nz: int = 64, dT: float = 1.0,
                             sigmaT: float = 0.01):
     """Two-layer thermocapillary channel (box 2 x 2 x 1 at 128 x 128 x 64).
