@@ -15,7 +15,9 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("precision", [cases.F64, cases.MIXED])
 def test_droplet_matches_oracle(precision):
     P = need_gpu()
-    p, s = cases.ma_bothe_droplet(n=32, precision=precision)
+    # the mixed form stores T in float: temperatures relative to 290 K
+    t_ref = 290.0 if precision == cases.MIXED else 0.0
+    p, s = cases.ma_bothe_droplet(n=32, precision=precision, t_ref=t_ref)
     p = p.replace(mg_fixed_cycles=8) if precision == cases.F64 else p
     if precision == cases.MIXED:
         s = cases.as_float32_state(s)
