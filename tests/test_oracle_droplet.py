@@ -42,3 +42,21 @@ def test_droplet_vortex_pair_upward_migration_and_symmetry():
     left, right = w[..., :half].sum(), w[..., half:].sum()
     assert left > 0.0 and right < 0.0
     assert abs(left + right) <= 1e-6 * abs(left)
+
+
+def test_temperature_reference_does_not_change_the_model():
+    """Storing temperatures relative to 290 K (what the mixed form wants)
+    gives the same flow and phase field, and the same temperature shifted by
+    290 K: only T - T0 enters the model."""
+    p0, s0 = cases.ma_bothe_droplet(n=16)
+    p1, s1 = cases.ma_bothe_droplet(n=16, t_ref=290.0)
+    a, b = dict(s0), dict(s1)
+    for q in range(4):
+        a, _ = O.step(a, p0, q, 0.0)
+        b, _ = O.step(b, p1, q, 0.0)
+    a = {k: np.asarray(v) for k, v in a.items()}
+    b = {k: np.asarray(v) for k, v in b.items()}
+    for k in ("u", "v", "alpha", "p"):
+        scale = np.abs(a[k]).max()
+        assert np.abs(a[k] - b[k]).max() <= 1e-9 * scale, k
+    assert np.abs((a["T"] - 290.0) - b["T"]).max() <= 1e-9
