@@ -62,7 +62,8 @@ typedef enum { FVM_TBC_NEUMANN = 0, FVM_TBC_DIRICHLET = 1 } fvm_tbc_kind;
 
 /* Parameters of the discrete method.  Sides are ordered -x,+x,-y,+y,-z,+z. */
 typedef struct {
-  int nx, ny, nz;            /* cells; a wall axis needs >= 4 cells             */
+  int nx, ny, nz;            /* cells; a wall axis needs >= 4 cells, a periodic */
+                             /* axis an even count or 1 (red-black colouring)   */
   double h;                  /* cell edge [m]                                   */
   int bc[3];                 /* fvm_bc_kind per axis x, y, z (no-slip walls)     */
   int tbc[6];                /* fvm_tbc_kind per side; Dirichlet on one axis max */
@@ -219,6 +220,16 @@ typedef enum {
 
 fvm_status fvm_profile(fvm_ctx* ctx, int on);
 fvm_status fvm_profile_read(fvm_ctx* ctx, int kernel_class, long* launches, double* total_ms);
+
+/* Fused multiply-add throughput of the current device (no counterpart in
+ * the paper; the peak against which kernels bound by arithmetic are
+ * reported).  precision FVM_F64 times double FMAs, FVM_MIXED float FMAs:
+ * eight independent register chains per thread over 8 blocks of 256 threads
+ * per SM, best of three timed launches after one warm-up launch, timed with
+ * CUDA events on cuda_stream (NULL = legacy default stream); synchronises the
+ * stream.  tflops: 2 flops per FMA / time; ms: the best launch time.  No
+ * device memory is allocated (the chains keep their result in registers). */
+fvm_status fvm_fma_peak(int precision, void* cuda_stream, double* tflops, double* ms);
 
 /* Number of CUDA kernels the context has launched (counted always, host
  * side); reset != 0 zeroes the counter after reading it. */

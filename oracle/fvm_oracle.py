@@ -76,6 +76,10 @@ class Grid:
         for d in range(3):
             if self.bc[d] == WALL and self.n[d] < 4:
                 raise ValueError("a wall axis needs at least 4 cells")
+            # the red-black colour (i + j + k) mod 2 of the smoother is a
+            # 2-colouring under wrap only for an even number of cells
+            if self.bc[d] == PERIODIC and self.n[d] > 1 and self.n[d] % 2:
+                raise ValueError("a periodic axis needs an even number of cells (or one)")
 
     @property
     def shape(self):

@@ -88,6 +88,10 @@ const char* check_params(const fvm_params* p) {
     if (p->bc[d] != FVM_BC_PERIODIC && p->bc[d] != FVM_BC_WALL) return "bc must be 0 or 1";
     int n = d == 0 ? p->nx : (d == 1 ? p->ny : p->nz);
     if (p->bc[d] == FVM_BC_WALL && n < 4) return "a wall axis needs >= 4 cells";
+    // red-black Gauss-Seidel colours cells by (i + j + k) mod 2, which is a
+    // 2-colouring under wrap only for an even cell count
+    if (p->bc[d] == FVM_BC_PERIODIC && n > 1 && n % 2)
+      return "a periodic axis needs an even number of cells (or one)";
     bool dl = p->tbc[2 * d] == FVM_TBC_DIRICHLET, dh = p->tbc[2 * d + 1] == FVM_TBC_DIRICHLET;
     if ((dl || dh) && p->bc[d] != FVM_BC_WALL) return "Dirichlet temperature needs a wall axis";
     if (dl || dh) ++ndir;

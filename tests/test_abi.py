@@ -60,7 +60,8 @@ def test_workspace_size_and_validation_on_host():
     assert n > 0
     bad = [p.replace(h=0.0), p.replace(nx=2), p.replace(precision=7), p.replace(rho=(0.0, 1.0)),
            p.replace(smooth_passes=3), p.replace(mg_levels=0),
-           p.replace(tbc=(1, 1, 1, 1, 0, 0), tbc_T0=(1.0,) * 6)]
+           p.replace(tbc=(1, 1, 1, 1, 0, 0), tbc_T0=(1.0,) * 6),
+           p.replace(nz=3), p.replace(bc=(0, 1, 0), nx=63)]   # odd periodic axes
     for q in bad:
         with pytest.raises(fvm.FvmError):
             fvm.fvm_workspace_size(q)
