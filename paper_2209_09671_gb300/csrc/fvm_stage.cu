@@ -330,8 +330,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     const int ox = d == 0, oy = d == 1, oz = d == 2;
     gv[d] = (S.a[Tile<3>::at(tx + ox, ty + oy, tz + oz)] - S.a[Tile<3>::at(tx - ox, ty - oy, tz - oz)]) * i2h;
     tv[d] = (S.s2[Tile<1>::at(tx + ox, ty + oy, tz + oz)] - S.s2[Tile<1>::at(tx - ox, ty - oy, tz - oz)]) * i2h;
-    sv[d] = (sigma_r(S.T[Tile<1>::at(tx + ox, ty + oy, tz + oz)], ph) -
-             sigma_r(S.T[Tile<1>::at(tx - ox, ty - oy, tz - oz)], ph)) * i2h;
+    const R Tp = S.T[Tile<1>::at(tx + ox, ty + oy, tz + oz)];
+    const R Tm = S.T[Tile<1>::at(tx - ox, ty - oy, tz - oz)];
+    // central difference of the sigma field (Eq. 5 as a cell field).  In
+    // float it is taken as dsigma/dT (T+ - T-), the same number for the
+    // linear sigma(T): the difference of two neighbouring temperatures is
+    // exact, while sigma0 + dsigma/dT (T - T0) rounded to float at
+    // sigma ~ 1.9 keeps only ~4 digits of a variation of ~1e-3
+    if (sizeof(R) == 4) sv[d] = ph.dsdT * (Tp - Tm) * i2h;
+    else sv[d] = (sigma_r(Tp, ph) - sigma_r(Tm, ph)) * i2h;
   }
   R gn = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
   R tn = sqrt(tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]) + epsn;

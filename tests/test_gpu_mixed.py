@@ -20,6 +20,12 @@ from tests.test_gpu_parity import _physics_case, _sphere
 pytestmark = pytest.mark.gpu
 
 TOL_MX = {"u": 1e-5, "v": 1e-5, "w": 1e-5, "p": 1e-5, "T": 1e-6, "alpha": 1e-6}
+# Both sides solve each projection to RTOL_CMP in mixed comparisons: a
+# solve stopped at ||b - L p|| <= rtol ||b|| can differ from another such
+# solve by up to cond(L) rtol in relative terms (about 1e6 rtol at density
+# ratio 7900 on 32^3), which at the default 1e-10 is as large as the bound
+# itself; at 1e-12 the comparison measures the float arithmetic alone.
+RTOL_CMP = 1e-12
 
 
 def _check(out, ref):
@@ -76,16 +82,17 @@ def test_mixed_static_drop():
 
 
 def test_mixed_melt_pool_small():
-    """Melt-pool surrogate physics (density ratio 7900) at 32^3, 3 steps."""
+    """Melt-pool surrogate physics (density ratio 7900) at 32^3, one step from
+    rest, both sides solved to RTOL_CMP, the bounds of TOL_MX."""
     P = need_gpu()
     p, s = cases.melt_pool(32, 32, 32, precision=cases.F64)
+    p = p.replace(mg_rtol=RTOL_CMP)
     s32d = {k: v.astype(np.float32).astype(np.float64) for k, v in s.items()}
     ref, rinfo = O.step(s32d, p, 0, 0.0)
     out, infos = gpu_step(P, p.replace(precision=cases.MIXED), s32d)
     assert infos[-1]["nan_flag"] == 0
-    errs = {k: rel_l2(out[k], ref[k].numpy()) for k in FIELDS}
-    assert errs["alpha"] <= 1e-6 and errs["T"] <= 1e-6, errs
-    assert max(errs["u"], errs["v"], errs["w"], errs["p"]) <= 1e-4, errs
+    assert max(infos[-1]["rel_residual"]) <= RTOL_CMP
+    _check(out, ref)
 
 
 def test_mixed_steps_replayed_as_graphs_match_eager_launches():
