@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "fvm_adjoint.h"
@@ -1172,22 +1173,27 @@ const char* fvm_version(void) { return "fvm-gb300 0.1"; }
 // the face coefficients, each level's correction, the reduction slots), and
 // calls that overlap on the GPU (other streams, other host threads) race on
 // the array.
+static constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
 constexpr int kNoAllocMaxDevices = 64;
 
-__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
 void* g_noalloc_ptr[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
 
-// device address of the scratch array on the current device (set up once)
+// device address of the scratch array on the current device (looked up once
+// per device, under a lock, so that host threads may make first calls
+// concurrently; the address stays valid until cudaDeviceReset on the device)
 fvm_status noalloc_scratch(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
     cudaGetLastError();
     return FVM_ECUDA;
   }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);

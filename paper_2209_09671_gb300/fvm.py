@@ -66,7 +66,7 @@ class fvm_step_info(ctypes.Structure):
 EXPORTS = ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step", "fvm_poisson_solve",
            "fvm_step_adjoint", "fvm_status_string", "fvm_last_error", "fvm_version",
            "fvm_profile", "fvm_profile_read", "fvm_launch_count", "fvm_poisson_solve_noalloc",
-           "fvm_stage_predict")
+           "fvm_stage_predict", "fvm_fma_peak")
 
 KERNEL_CLASSES = ("smooth", "interface", "scalars", "momentum", "div_rhs", "beta", "gs_fine",
                   "gs_coarse", "restrict_fine", "restrict_coarse", "prolong_fine",
@@ -110,11 +110,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_void_p]
     lib.fvm_poisson_solve_noalloc.argtypes = [P(fvm_params), ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, P(fvm_step_info)]
+    lib.fvm_fma_peak.argtypes = [ctypes.c_int, ctypes.c_void_p, P(ctypes.c_double),
+                                 P(ctypes.c_double)]
     lib.fvm_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_long),
                                      P(ctypes.c_double)]
     for name in ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step",
                  "fvm_poisson_solve", "fvm_step_adjoint", "fvm_profile", "fvm_profile_read", "fvm_launch_count",
-                 "fvm_poisson_solve_noalloc", "fvm_stage_predict"):
+                 "fvm_poisson_solve_noalloc", "fvm_stage_predict", "fvm_fma_peak"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -305,15 +307,39 @@ def fvm_poisson_solve_noalloc(params, alpha, rhs, p, stream=None) -> dict:
     import torch
     lib = load()
     cp = params if isinstance(params, fvm_params) else make_params(params)
-    if stream is None:
-        stream = torch.cuda.current_stream(p.device)
-    inf = fvm_step_info()
-    rc = lib.fvm_poisson_solve_noalloc(ctypes.byref(cp), ctypes.c_void_p(alpha.data_ptr()),
-                                       ctypes.c_void_p(rhs.data_ptr()), ctypes.c_void_p(p.data_ptr()),
-                                       ctypes.c_void_p(stream.cuda_stream), ctypes.byref(inf))
+    n = int(cp.nx) * int(cp.ny) * int(cp.nz)
+    adt = torch.float32 if int(cp.precision) == MIXED else torch.float64
+    for name, t, dt in (("alpha", alpha, adt), ("rhs", rhs, torch.float64), ("p", p, torch.float64)):
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous() and t.device == p.device):
+            raise ValueError(f"{name} must be a contiguous {dt} tensor on {p.device}")
+        if t.numel() != n:
+            raise ValueError(f"{name} must hold nx*ny*nz = {n} elements")
+    with torch.cuda.device(p.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(p.device)
+        inf = fvm_step_info()
+        rc = lib.fvm_poisson_solve_noalloc(ctypes.byref(cp), ctypes.c_void_p(alpha.data_ptr()),
+                                           ctypes.c_void_p(rhs.data_ptr()),
+                                           ctypes.c_void_p(p.data_ptr()),
+                                           ctypes.c_void_p(stream.cuda_stream), ctypes.byref(inf))
     out = inf.as_dict()
     out["status"] = rc
     return out
+
+
+def fvm_fma_peak(precision: int, stream=None) -> dict:
+    """Measured FMA throughput of the current device in double (F64) or
+    float (MIXED): {"tflops": ..., "ms": ...}."""
+    import torch
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib.fvm_fma_peak(int(precision), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(tf),
+                          ctypes.byref(ms))
+    if rc != FVM_OK:
+        raise FvmError(rc, "fvm_fma_peak failed")
+    return {"tflops": tf.value, "ms": ms.value}
 
 
 def to_device(state: dict, mixed: bool, device="cuda") -> dict:

@@ -53,6 +53,6 @@ def test_noalloc_matches_workspace_solve_twice(precision):
 def test_noalloc_rejects_grids_beyond_its_scratch():
     P = need_gpu()
     p = cases.Params(nx=128, ny=128, nz=128, h=1.0 / 128, bc=(1, 1, 1))
-    t = torch.zeros(8, dtype=torch.float64, device="cuda")
+    t = torch.zeros(p.shape, dtype=torch.float64, device="cuda")
     got = P.fvm.fvm_poisson_solve_noalloc(p, t, t, t)
     assert got["status"] == P.fvm.FVM_ENOMEM
