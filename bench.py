@@ -34,36 +34,65 @@ UNIT = "cell-updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM = 6800.0
-# nominal dense FP64 rate of a GB300 (the pool's profiling recipe table), for
-# kernels bound by the FP64 pipe
-NOMINAL_FP64_TFLOPS = 1.25
 # FP64 flops per cell of one launch of an FP64-bound class: the mixed-form
-# residual takes per coupled face a difference and an FMA (3 flops, 6 faces),
-# then b - w*acc and the r^2 accumulation (2 + 2)
+# residual takes per coupled face a difference and an FMA (2 flops + 1, 6
+# faces), then b - w*acc and the r^2 accumulation (2 + 2)
 FP64_FLOPS_PER_CELL = {"residual64": 22}
 
-# algorithmic bytes per cell of one launch of a fine-level kernel class, for
-# element size s (4 mixed, 8 double) and beta size bs; the derivation of each
-# figure is in the design notes (every array a kernel must touch, streamed once)
+
 def alg_bytes_per_cell(cls: str, mixed: bool) -> float | None:
+    """Algorithmic bytes per cell of one launch, counted the way the
+    measurement plan counts them: one smoothing sweep (both colours) touches
+    p (read and write), b and alpha, 4 accesses, so one colour launch is 2
+    accesses; the residual restriction p, b, alpha and 1/8 of a coarse
+    value; the prolongation 1/8 coarse and p read and written; the stage
+    kernels every field they must read or write once.  s = 4 (mixed) or
+    8 (FP64); the double projection fields (b, p) are 8 in both forms."""
     s = 4 if mixed else 8
-    bs = s
     table = {
-        "gs_fine": 2 * s + s + 3 * bs,          # one colour sweep: x read+write, b, three betas
+        "gs_fine": 2 * s,                        # one colour: half of (p r+w, b, alpha)
+        "gs_fused_pre": 4 * s,                   # fused sweeps: p r+w, b, alpha once per launch
+        "gs_fused_post": 4 * s + s / 8,          # ... and the coarse correction (1/8)
+        "restrict_fine": 3 * s + s / 8,
+        "prolong_fine": 2 * s + s / 8,
         "momentum": 9 * s + 3 * s,               # u,v,w,alpha,T,kappa,M0..2 in; u*,v*,w* out
         "scalars": 7 * s + 2 * s,                # u,v,w,alpha,T,Sn alpha,Sn T in; alpha,T out
-        "interface": 2 * s + 4 * s,              # alpha, T in; kappa, M out (smoothing stays on chip)
+        "interface": 2 * s + 4 * s,              # alpha, T in; kappa, M out
         "smooth": 2 * s,
         "div_rhs": 3 * s + 8,
-        "correct": 6 * s + 8 + 3 * bs + 3 * s,   # u*, Sn u, p, beta in; u out
-        "residual64": 8 + 8 + 3 * 4 + 4,         # p, b, float beta in; float r out
+        "correct": 6 * s + 8 + s + 3 * s,        # u*, Sn u, p, alpha in; u out
+        "residual64": 8 + 8 + 4 + 4,             # p, b, alpha in; float r out
         "add_correction": 8 + 4 + 8,
-        "restrict_fine": 2 * s + s + 3 * bs + 2 * s / 8,
-        "prolong_fine": 2 * s + s / 8,
-        "resnorm": 2 * s + 3 * bs,
-        "beta": s + 3 * bs,
+        "beta": s + 3 * s,
     }
     return table.get(cls)
+
+
+def compulsory_bytes_per_cell(cls: str, mixed: bool) -> float | None:
+    """Bytes per cell each launch must move with the data layout of the
+    library (three stored face-coefficient arrays beta instead of alpha,
+    colour-strided sweeps that stream every cache line of x and b)."""
+    s = 4 if mixed else 8
+    table = {
+        "gs_fine": 2 * s + s + 3 * s,            # x read+write, b, three betas
+        "gs_fused_pre": 2 * s + s + 3 * s,
+        "gs_fused_post": 2 * s + s + 3 * s + s / 8,
+        "restrict_fine": 2 * s + s + 3 * s + 2 * s / 8,
+        "prolong_fine": 2 * s + s / 8,
+        "residual64": 8 + 8 + 3 * 4 + 4,         # p, b, float beta in; float r out
+        "correct": 6 * s + 8 + 3 * s + 3 * s,    # u*, Sn u, p, beta in; u out
+        "beta": s + 3 * s,
+    }
+    return table.get(cls, alg_bytes_per_cell(cls, mixed))
+
+
+def whole_step_alg_bytes(mixed: bool, nbar_v: float, n_outer: float) -> float:
+    """Algorithmic bytes per cell of one full step (three stages) with
+    nbar_v V-cycles and n_outer double refinements per stage: mixed
+    3 (120 + 100 nbar_v + 40 n_outer), FP64 3 (208 + 195 nbar_v)."""
+    if mixed:
+        return 3.0 * (120.0 + 100.0 * nbar_v + 40.0 * n_outer)
+    return 3.0 * (208.0 + 195.0 * nbar_v)
 
 
 def parse():
@@ -82,6 +111,10 @@ def parse():
     ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the mixed-against-FP64 error report at 64^3")
+    ap.add_argument("--channel-steps", type=int, default=20,
+                    help="steps of the thermocapillary-channel side measurement (0: skip)")
     ap.add_argument("--mx-inner", type=int, default=None,
                     help="float V-cycles per double refinement of the mixed solve (default: the "
                          "workload's, 2)")
@@ -124,9 +157,11 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_for(cls: str, mixed: bool):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernels changed since it was taken."""
+def traffic_for(cls: str, mixed: bool, ncells: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled from the
+    captured grid to ncells cells (the traffic of these kernels grows in
+    proportion to the cells), or None when the kernels changed since it was
+    taken."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
@@ -136,7 +171,9 @@ def traffic_for(cls: str, mixed: bool):
         return None
     key = f"{cls}/{'mixed' if mixed else 'f64'}"
     v = d.get("per_launch_bytes", {}).get(key)
-    return float(v) if v is not None else None
+    if v is None:
+        return None
+    return float(v) * ncells / float(d.get("cells", 256 ** 3))
 
 
 class ClockSampler:
@@ -190,14 +227,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
-def cpu_oracle_sample(target_s: float = 15.0):
+def cpu_oracle_sample(target_s: float = 12.0, threads: int | None = None):
     """The FP64 oracle on the host cores: melt-pool recipe (same h, physics and
-    seed) at 48^3, as many steps as fit in about target_s seconds (1 to 24)."""
+    seed) at 48^3, as many steps as fit in about target_s seconds (1 to 24),
+    with `threads` torch threads (None: all the host's cores)."""
     import torch
 
     import cases
     from oracle import fvm_oracle as O
     n = 48
+    before = torch.get_num_threads()
+    nthreads = threads if threads else (os.cpu_count() or before)
+    torch.set_num_threads(nthreads)
     p, s = cases.melt_pool(n, n, n, precision=cases.F64)
     t0 = time.perf_counter()
     st = s
@@ -208,10 +249,21 @@ def cpu_oracle_sample(target_s: float = 15.0):
         if time.perf_counter() - t0 >= target_s or steps >= 24:
             break
     el = time.perf_counter() - t0
-    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": torch.get_num_threads(),
-            "kind": "oracle",
+    used = torch.get_num_threads()
+    torch.set_num_threads(before)
+    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": used,
+            "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"FP64 oracle, melt-pool recipe at {n}^3 (h, physics, seed of the 256^3 "
-                      f"workload), {steps} full steps in {el:.1f} s"}
+                      f"workload), {steps} full steps in {el:.1f} s on {used} thread(s)"}
+
+
+def cpu_baselines():
+    """The oracle sample at the host's core count (the reported baseline) and
+    at one thread beside it."""
+    full = cpu_oracle_sample(12.0, None)
+    one = cpu_oracle_sample(8.0, 1)
+    full["single_thread"] = {k: one[k] for k in ("value", "cores", "sample")}
+    return full
 
 
 def run_reference(args, rank, world):
@@ -469,6 +521,73 @@ def whole_job_rate(cells_per_rank: int, world: int, seconds: float) -> float:
     return world * cells_per_rank / seconds
 
 
+def mixed_vs_f64_errors(P, dev, stream, n=64):
+    """Per-field relative L2 of one mixed step against one FP64 step from the
+    same float-rounded state (the n^3 melt-pool recipe after four FP64 steps,
+    both solved to 1e-10), with max |D u| dt of each; the FP64 GPU step
+    equals the FP64 oracle to 1e-11 (parity tests), so it stands in for it."""
+    import numpy as np
+    import torch
+
+    import cases
+    p, s = cases.melt_pool(n, n, n, precision=cases.F64)
+    with torch.cuda.stream(stream):
+        sol = P.Solver(p, device=dev, stream=stream)
+        st = P.to_device(s, False, dev)
+        for q in range(4):
+            sol.fvm_step(st, q, 0.0, info=False)
+        s32 = {k: (v.clone() if k == "p" else v.float().double()) for k, v in st.items()}
+        a = {k: v.clone() for k, v in s32.items()}
+        inf64 = sol.fvm_step(a, 4, 0.0, info=True)
+        sol.close()
+        solm = P.Solver(p.replace(precision=cases.MIXED), device=dev, stream=stream)
+        b = {k: (v.clone() if k == "p" else v.float()) for k, v in s32.items()}
+        infm = solm.fvm_step(b, 4, 0.0, info=True)
+        solm.close()
+    stream.synchronize()
+    errs = {}
+    for k in ("u", "v", "w", "p", "T", "alpha"):
+        ref = a[k]
+        nr = ref.norm().item()
+        errs[k] = (b[k].double() - ref).norm().item() / nr if nr > 0 else None
+    return {"grid": [n, n, n], "rel_l2_mixed_vs_f64": errs,
+            "max_div_dt": {"mixed": infm["max_div_dt"], "f64": inf64["max_div_dt"]},
+            "rel_residual": {"mixed": infm["rel_residual"], "f64": inf64["rel_residual"]},
+            "reference": "the FP64 GPU step (equal to the FP64 oracle to 1e-11 in the parity "
+                         "tests) from the same float-rounded state"}
+
+
+def channel_side(P, dev, stream, steps):
+    """The two-layer thermocapillary channel at 128 x 128 x 64: FP64 and mixed
+    steps from its conduction state, cell-updates per second of each."""
+    import torch
+
+    import cases
+    out = {"grid": [128, 128, 64], "steps": steps}
+    for name, prec in (("mixed", cases.MIXED), ("f64", cases.F64)):
+        p, s = cases.thermocapillary_channel()
+        p = p.replace(precision=prec)
+        with torch.cuda.stream(stream):
+            sol = P.Solver(p, device=dev, stream=stream)
+            st = P.to_device(s, prec == cases.MIXED, dev)
+            for q in range(3):
+                sol.fvm_step(st, q, 0.0, info=False)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for q in range(steps):
+                sol.fvm_step(st, 3 + q, 0.0, info=False)
+            e1.record(stream)
+            stream.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / steps
+            info = sol.fvm_step(st, 3 + steps, 0.0, info=True)
+            sol.close()
+        out[name] = {"value": p.ncells / t, "ms_per_step": t * 1e3,
+                     "vcycles_last_step": info["vcycles"], "max_div_dt": info["max_div_dt"],
+                     "rel_residual": info["rel_residual"]}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -484,6 +603,11 @@ def run_ours(args, rank, world, local_rank):
     def barrier():
         ranks_barrier()
 
+    stream = torch.cuda.Stream(device=dev)
+    # measured arithmetic peaks of this GPU (kernels bound by the FMA pipes)
+    fma64 = P.fvm.fvm_fma_peak(P.F64, stream)
+    fma32 = P.fvm.fvm_fma_peak(P.MIXED, stream)
+
     # ---------------- mixed-precision step (the headline) -------------------
     p, s0 = make_workload(shape, cases.MIXED, args.mg_levels)
     if args.mx_inner:
@@ -492,7 +616,6 @@ def run_ours(args, rank, world, local_rank):
         p = p.replace(mg_pre=args.mg_pre)
     if args.mg_post is not None:
         p = p.replace(mg_post=args.mg_post)
-    stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         solver = P.Solver(p, device=dev, stream=stream)
         state = P.to_device(s0, True, dev)
@@ -518,6 +641,7 @@ def run_ours(args, rank, world, local_rank):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = solver.fvm_launch_count()
     clk = clocks.stop()
+    max_dT = (state["T"].double() - p.T0).abs().max().item()
     # per-kernel durations: the same workload continued for as many steps,
     # every launch bracketed by CUDA events on the solver's stream (eager
     # launches: event timing replaces the graph replay of the refinement loop)
@@ -549,17 +673,22 @@ def run_ours(args, rank, world, local_rank):
         if cls in FP64_FLOPS_PER_CELL:
             flops = FP64_FLOPS_PER_CELL[cls] * N
             achieved = flops / per_launch_s / 1e12
-            return dict(bound="alu", achieved=achieved, peak=NOMINAL_FP64_TFLOPS,
-                        peak_kind="nominal FP64 rate (no measured FP64 peak)", unit="TFLOP/s",
-                        frac=achieved / NOMINAL_FP64_TFLOPS, traffic=traffic_for(cls, True),
-                        alg_flops_per_launch=flops, **common)
+            return dict(bound="alu", achieved=achieved, peak=fma64["tflops"],
+                        peak_kind="measured FP64 FMA throughput of this GPU (fvm_fma_peak)",
+                        unit="TFLOP/s", frac=achieved / fma64["tflops"],
+                        traffic=traffic_for(cls, True, N), alg_flops_per_launch=flops, **common)
         bpc = alg_bytes_per_cell(cls, True)
         if bpc is None:
             return None
+        cpc = compulsory_bytes_per_cell(cls, True)
         achieved = bpc * N / per_launch_s / 1e9
+        traffic = traffic_for(cls, True, N)
         return dict(bound="hbm", achieved=achieved, peak=peak,
                     peak_kind=f"{peak_kind} copy bandwidth", unit="GB/s", frac=achieved / peak,
-                    traffic=traffic_for(cls, True), alg_bytes_per_launch=bpc * N, **common)
+                    traffic=traffic, alg_bytes_per_launch=bpc * N,
+                    compulsory_bytes_per_launch=cpc * N,
+                    frac_at_compulsory_bytes=cpc * N / per_launch_s / 1e9 / peak,
+                    traffic_alg_ratio=(traffic / (bpc * N)) if traffic else None, **common)
 
     ranked = sorted(((k, v) for k, v in prof.items() if v[0]), key=lambda kv: -kv[1][1])
     roof = roofline_of(ranked[0][0], *ranked[0][1]) if ranked else None
@@ -570,6 +699,14 @@ def run_ours(args, rank, world, local_rank):
             break
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3),
                    "share": round(v[1] / 1e3 / prof_elapsed, 4)} for k, v in prof.items() if v[0]}
+    n_outer = sum(info["vcycles"]) / 3.0
+    nbar_v = n_outer * p.mx_inner_cycles
+    b_step = whole_step_alg_bytes(True, nbar_v, n_outer)
+    whole = {"alg_bytes_per_cell": b_step, "nbar_v": nbar_v, "n_outer": n_outer,
+             "achieved": b_step * N / t_step / 1e9, "peak": peak, "unit": "GB/s",
+             "frac": b_step * N / t_step / 1e9 / peak,
+             "formula": "3 (120 + 100 nbar_v + 40 n_outer) bytes per cell and step, nbar_v and "
+                        "n_outer from the last step's refinement counts"}
 
     # ---------------- end to end through host buffers -------------------------
     e2e = None
@@ -618,7 +755,6 @@ def run_ours(args, rank, world, local_rank):
             st64 = P.to_device(s64, False, dev)
         sol64.fvm_step(st64, 0, 0.0, info=False)
         stream.synchronize()
-        sol64.fvm_profile(True)
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         for q in range(args.f64_steps):
@@ -626,19 +762,30 @@ def run_ours(args, rank, world, local_rank):
         a1.record(stream)
         stream.synchronize()
         t64 = max_over_ranks(a0.elapsed_time(a1) / 1e3 / args.f64_steps, dev)
+        sol64.fvm_profile(True)
+        sol64.fvm_step(st64, 1 + args.f64_steps, 0.0, info=False)
         prof64 = sol64.fvm_profile_read()
-        inf64 = sol64.fvm_step(st64, 1 + args.f64_steps, 0.0, info=True)
-        f64 = {"value": whole_job_rate(N, world, t64), "ms_per_step": t64 * 1e3, "steps": args.f64_steps,
-               "vcycles_last_step": inf64["vcycles"],
-               "kernels_ms": {k: round(v[1], 2) for k, v in prof64.items() if v[0]},
-               "bound": "alu (FP64 units)"}
+        sol64.fvm_profile(False)
+        inf64 = sol64.fvm_step(st64, 2 + args.f64_steps, 0.0, info=True)
+        nv64 = sum(inf64["vcycles"]) / 3.0
+        b64 = whole_step_alg_bytes(False, nv64, 0)
+        f64 = {"value": whole_job_rate(N, world, t64), "ms_per_step": t64 * 1e3,
+               "steps": args.f64_steps, "vcycles_last_step": inf64["vcycles"],
+               "max_div_dt": inf64["max_div_dt"], "rel_residual": inf64["rel_residual"],
+               "kernels_ms_one_step": {k: round(v[1], 2) for k, v in prof64.items() if v[0]},
+               "whole_step": {"alg_bytes_per_cell": b64, "nbar_v": nv64,
+                              "frac": b64 * N / t64 / 1e9 / peak},
+               "bound": "FP64 FMA pipe"}
         sol64.close()
         del st64, sol64
         torch.cuda.empty_cache()
 
+    accuracy = None if args.no_accuracy else mixed_vs_f64_errors(P, dev, stream)
+    channel = None if args.channel_steps <= 0 else channel_side(P, dev, stream, args.channel_steps)
+
     if rank != 0:
         return
-    cpu = None if args.no_cpu else cpu_oracle_sample()
+    cpu = None if args.no_cpu else cpu_baselines()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
@@ -653,11 +800,18 @@ def run_ours(args, rank, world, local_rank):
                    "l2": f"inputs larger than L2 (state {N * 28 / 2**20:.0f} MiB)"},
         "roofline": roof,
         "roofline_top_hbm_kernel": hbm_top,
+        "roofline_whole_step": whole,
+        "fma_peaks_tflops": {"f64": fma64["tflops"], "f32": fma32["tflops"],
+                             "how": "fvm_fma_peak: 8 independent FMA chains per thread, "
+                                    "8 x 256 threads per SM, best of 3 launches"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
         "f64": f64,
+        "accuracy_64cubed": accuracy,
+        "channel_128x128x64": channel,
+        "max_abs_T_minus_T0_after_timed_steps_K": max_dT,
         "last_step_info": info,
         "kernels": kernels,
     }

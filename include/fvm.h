@@ -160,8 +160,10 @@ fvm_status fvm_poisson_solve(fvm_ctx* ctx, const void* alpha, const double* rhs,
  * Same arithmetic and status codes as fvm_poisson_solve (no fvm_last_error
  * message: there is no context).  The first call on a device looks up the
  * array's device address with cudaGetSymbolAddress, so make it before any
- * stream capture on that device.  Every call shares the array; calls that
- * overlap on the GPU (several streams or host threads at once) race. */
+ * stream capture on that device; the address is kept until the process
+ * exits and is not valid after a cudaDeviceReset of that device.  Every call
+ * shares the array; calls that overlap on the GPU (several streams or host
+ * threads at once) race. */
 fvm_status fvm_poisson_solve_noalloc(const fvm_params* prm, const void* alpha,
                                      const double* rhs, double* p, void* cuda_stream,
                                      fvm_step_info* info);

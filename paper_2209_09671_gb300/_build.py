@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfvm.so")
-SOURCES = ("fvm_api.cu", "fvm_stage.cu", "fvm_mg.cu", "fvm_adjoint.cu")
+SOURCES = ("fvm_api.cu", "fvm_stage.cu", "fvm_mg.cu", "fvm_adjoint.cu", "fvm_measure.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
