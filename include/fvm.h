@@ -24,11 +24,20 @@
  *            workspace of fvm_workspace_size() bytes to fvm_create() and
  *            keeps it alive until fvm_destroy().  The library never frees
  *            caller memory.
- *  Streams   work is enqueued on the stream given to fvm_create().  A call
- *            returns after the host has read what it needs (the residual
- *            norm of each multigrid cycle unless mg_fixed_cycles > 0, and
- *            the diagnostics when info != NULL); device work may still be
- *            running otherwise.
+ *  Streams   work is enqueued on the stream given to fvm_create().
+ *            fvm_step and fvm_poisson_solve with info == NULL return without
+ *            waiting for the device: each pressure solve runs as one CUDA
+ *            graph whose stopping test (||b - L p|| <= mg_rtol ||b||, or
+ *            mg_fixed_cycles cycles) is taken on the device by a conditional
+ *            loop node, so the host never reads a residual.  A solve that
+ *            stops at mg_max_cycles above mg_rtol or meets a non-finite norm
+ *            is then recorded on the device and reported by fvm_sync().  With
+ *            info != NULL the call waits once, at its end, and returns that
+ *            status itself.  The first solve with a given p pointer builds
+ *            its graph (stream capture on the context's stream, so that
+ *            stream must not be capturing then); while profiling is on
+ *            (fvm_profile) the solves run as eager launches with a host
+ *            loop instead.
  *  Errors    functions return an fvm_status; no C++ exception, abort or
  *            device trap crosses the ABI.  fvm_last_error() gives a message.
  *  Precision FVM_F64: u, v, w, alpha, T are double.  FVM_MIXED: they are
@@ -130,6 +139,11 @@ fvm_status fvm_destroy(fvm_ctx* ctx);
  * info may be NULL.  Returns FVM_ENOCONV / FVM_EUNSTABLE as documented. */
 fvm_status fvm_step(fvm_ctx* ctx, fvm_state* st, long step_index, double dt,
                     fvm_step_info* info);
+
+/* Wait for the context's stream and return the worst status recorded by
+ * the device-side pressure solves since the previous fvm_sync (FVM_ENOCONV
+ * or FVM_EUNSTABLE; FVM_OK if none), clearing it. */
+fvm_status fvm_sync(fvm_ctx* ctx);
 
 /* The density-weighted pressure solve alone: L p = rhs with
  * (L p)_c = sum_faces beta_f (p_c - p_nb)/h^2, beta_f = 2/(rho_L + rho_R) from

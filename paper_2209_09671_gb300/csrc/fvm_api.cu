@@ -171,10 +171,17 @@ struct fvm_ctx {
   cudaEvent_t* prof_ev;      // 2 * kProfSlots events
   int* prof_cls;
   long nlaunch;              // kernels launched since the last count reset
-  // CUDA graphs of the mixed-form refinement iteration, keyed by (p, alpha)
+  // CUDA graphs of the whole pressure solve with its stopping test on the
+  // device (a conditional WHILE node), keyed by the solution pointer p
   int graphs_ok;             // 1: try stream capture; 0: eager launches only
-  struct GEntry { const void* p; const void* a; cudaGraphExec_t exec; long nk; } gcache[6];
+  struct GEntry { const void* p; cudaGraphExec_t exec; long nk; } gcache[8];
   int gnext;
+  long nk_body;              // kernels of one cycle (refinement) of a graph's loop
+  SolveCtl* ctl;             // device: controller of the solve in flight
+  SolveCtl* rec;             // device: kRecords records (stages 0..2, lone solve 3)
+  int* sticky;               // device: worst status of graph solves since fvm_sync
+  unsigned long long* runs;  // device: loop cycles run by graph solves
+  unsigned long long runs_base;  // value of *runs at the last launch-count reset
   long prof_launches[FVM_KCLASS_COUNT];
   double prof_ms[FVM_KCLASS_COUNT];
   char err[512];
@@ -183,6 +190,7 @@ struct fvm_ctx {
 namespace {
 
 constexpr int kProfSlots = 4096;
+constexpr int kRecords = 4;   // solve records: the three stages of a step, a lone solve
 
 void prof_fold(fvm_ctx* c) {
   if (!c->prof_n) return;
@@ -259,6 +267,7 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
   size_t o_flags = pl.take(8 * sizeof(int));
   size_t o_dt = pl.take(2 * sizeof(double));   // dt and 1/dt
   size_t o_lim = pl.take(sizeof(int));
+  size_t o_ctl = pl.take((1 + kRecords) * sizeof(SolveCtl) + sizeof(int) + sizeof(unsigned long long));
   constexpr int kAdjFields = 18;
   size_t o_adj[kAdjFields];
   size_t o_K = 0;
@@ -294,6 +303,10 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
     c->flags = (int*)(w + o_flags);
     c->dt_dev = (double*)(w + o_dt);
     c->lim_dev = (int*)(w + o_lim);
+    c->ctl = (SolveCtl*)(w + o_ctl);
+    c->rec = c->ctl + 1;
+    c->runs = (unsigned long long*)(c->rec + kRecords);
+    c->sticky = (int*)(c->runs + 1);
     if (p.adjoint) {
       double* a[kAdjFields];
       for (int q = 0; q < kAdjFields; ++q) a[q] = (double*)(w + o_adj[q]);
@@ -486,9 +499,7 @@ fvm_status solve_f64(fvm_ctx* c, double* p, double* b, int* cycles_out, double* 
 // MIXED: double defect correction around float V-cycles.  One refinement
 // iteration is: e = 0; mx_inner_cycles float V-cycles on L e = r; p += e;
 // r = b - L p in double (stored as float for the next iteration) and its
-// norm.  It has no host synchronisation, so after the first use it is
-// replayed as a CUDA graph (keyed by the p and alpha pointers) unless
-// profiling is on or the stream cannot be captured.
+// norm.
 void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, double* b,
                  float* const* be, double crtol) {
   cudaStream_t s = c->stream;
@@ -497,43 +508,6 @@ void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, 
   for (int q = 0; q < c->prm.mx_inner_cycles; ++q) vcycle<float>(c, Ls, 0, crtol);
   TIMED(c, FVM_K_ADD_CORRECTION, 1, launch_add_correction(N, p, c->e32, s));
   TIMED(c, FVM_K_RESIDUAL64, 2, launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, s));
-}
-
-cudaGraphExec_t refine_graph(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p,
-                             double* b, float* const* be, double crtol, long* nk) {
-  for (int q = 0; q < 6; ++q)
-    if (c->gcache[q].exec && c->gcache[q].p == p && c->gcache[q].a == alpha) {
-      *nk = c->gcache[q].nk;
-      return c->gcache[q].exec;
-    }
-  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    cudaGetLastError();
-    c->graphs_ok = 0;
-    return nullptr;
-  }
-  const long n0 = c->nlaunch;
-  refine_once(c, Ls, alpha, p, b, be, crtol);
-  const long captured = c->nlaunch - n0;
-  c->nlaunch = n0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  if (cudaStreamEndCapture(c->stream, &graph) != cudaSuccess || !graph ||
-      cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-    cudaGetLastError();
-    if (graph) cudaGraphDestroy(graph);
-    c->graphs_ok = 0;
-    return nullptr;
-  }
-  cudaGraphDestroy(graph);
-  auto& slot = c->gcache[c->gnext];
-  if (slot.exec) cudaGraphExecDestroy(slot.exec);
-  slot.p = p;
-  slot.a = alpha;
-  slot.exec = exec;
-  slot.nk = captured;
-  c->gnext = (c->gnext + 1) % 6;
-  *nk = captured;
-  return exec;
 }
 
 fvm_status solve_mixed(fvm_ctx* c, const float* alpha, double* p, double* b, int* cycles_out,
@@ -579,15 +553,7 @@ fvm_status solve_mixed(fvm_ctx* c, const float* alpha, double* p, double* b, int
       if (!isfinite(rel)) return set_err(c, FVM_EUNSTABLE, "non-finite pressure residual");
       if (rel <= c->prm.mg_rtol || outer >= c->prm.mg_max_cycles) break;
     }
-    cudaGraphExec_t exec = nullptr;
-    long nk = 0;
-    if (c->graphs_ok && !c->prof) exec = refine_graph(c, Ls, alpha, p, b, be, crtol, &nk);
-    if (exec) {
-      if (cudaGraphLaunch(exec, s) != cudaSuccess) return cuda_check(c, "graph launch");
-      c->nlaunch += nk;
-    } else {
-      refine_once(c, Ls, alpha, p, b, be, crtol);
-    }
+    refine_once(c, Ls, alpha, p, b, be, crtol);
     ++outer;
   }
   TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(p, N, false, c->partial, c->scal + 2, s));
@@ -597,6 +563,188 @@ fvm_status solve_mixed(fvm_ctx* c, const float* alpha, double* p, double* b, int
   st = cuda_check(c, "mixed pressure solve");
   if (st) return st;
   if (fixed == 0 && rel > c->prm.mg_rtol)
+    return set_err(c, FVM_ENOCONV, "pressure solve reached mg_max_cycles above mg_rtol");
+  return FVM_OK;
+}
+
+// ----- the pressure solve as one CUDA graph ----------------------------------
+// prologue: coarse betas, controller reset, ||b||^2, the first residual norm
+// and the first stopping test; loop (conditional WHILE node): one cycle (F64)
+// or refinement (MIXED), its residual norm, the stopping test; epilogue: zero
+// p for a zero right-hand side, remove the mean of p.  The same kernels in
+// the same order as the host loops of solve_f64 / solve_mixed, so the
+// results agree bit for bit; only the test is taken on the device.
+void graph_prologue(fvm_ctx* c, double* p, cudaGraphConditionalHandle h) {
+  cudaStream_t s = c->stream;
+  const long long N = c->g.N;
+  const int fixed = c->prm.mg_fixed_cycles;
+  if (c->mixed) {
+    MGLevel<float> Ls[kMaxLevels];
+    float* be[3] = {(float*)c->beta0[0], (float*)c->beta0[1], (float*)c->beta0[2]};
+    hierarchy<float>(c, c->e32, c->r32, be, Ls);
+    coarsen_betas<float>(c, Ls);
+    TIMED(c, FVM_K_MISC, 1, launch_ctl_reset(c->ctl, s));
+    TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(c->b, N, true, c->partial, c->scal + 0, s));
+    TIMED(c, FVM_K_RESIDUAL64, 2,
+          launch_residual64(c->g, p, c->b, be, c->r32, c->partial, c->scal + 1, s));
+  } else {
+    MGLevel<double> Ls[kMaxLevels];
+    double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};
+    hierarchy<double>(c, p, c->b, be, Ls);
+    coarsen_betas<double>(c, Ls);
+    TIMED(c, FVM_K_MISC, 1, launch_ctl_reset(c->ctl, s));
+    TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(c->b, N, true, c->partial, c->scal + 0, s));
+    TIMED(c, FVM_K_RESNORM, 2, launch_residual_norm2<double>(Ls[0], c->partial, c->scal + 1, s));
+  }
+  TIMED(c, FVM_K_MISC, 1,
+        launch_ctl_step(h, c->ctl, c->scal + 0, c->scal + 1, c->prm.mg_rtol, c->prm.mg_max_cycles,
+                        fixed, c->runs, s));
+}
+
+void graph_body(fvm_ctx* c, double* p, cudaGraphConditionalHandle h) {
+  cudaStream_t s = c->stream;
+  const int fixed = c->prm.mg_fixed_cycles;
+  if (c->mixed) {
+    MGLevel<float> Ls[kMaxLevels];
+    float* be[3] = {(float*)c->beta0[0], (float*)c->beta0[1], (float*)c->beta0[2]};
+    hierarchy<float>(c, c->e32, c->r32, be, Ls);
+    const double crtol = c->prm.coarse_rtol > 1e-6 ? c->prm.coarse_rtol : 1e-6;
+    refine_once(c, Ls, nullptr, p, c->b, be, crtol);
+  } else {
+    MGLevel<double> Ls[kMaxLevels];
+    double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};
+    hierarchy<double>(c, p, c->b, be, Ls);
+    vcycle<double>(c, Ls, 0, c->prm.coarse_rtol);
+    TIMED(c, FVM_K_RESNORM, 2, launch_residual_norm2<double>(Ls[0], c->partial, c->scal + 1, s));
+  }
+  TIMED(c, FVM_K_MISC, 1,
+        launch_ctl_step(h, c->ctl, c->scal + 0, c->scal + 1, c->prm.mg_rtol, c->prm.mg_max_cycles,
+                        fixed, c->runs, s));
+}
+
+void graph_epilogue(fvm_ctx* c, double* p) {
+  cudaStream_t s = c->stream;
+  const long long N = c->g.N;
+  TIMED(c, FVM_K_MISC, 1, launch_zero_if_rhs_zero(c->ctl, p, N, s));
+  TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(p, N, false, c->partial, c->scal + 2, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sub_mean(p, N, c->scal + 2, s));
+}
+
+// the solve graph for solution pointer p (built on first use, cached); null
+// when graphs are unavailable (the caller then runs the host loop)
+cudaGraphExec_t solve_graph(fvm_ctx* c, double* p, long* nk_fixed) {
+  for (int q = 0; q < 8; ++q)
+    if (c->gcache[q].exec && c->gcache[q].p == p) {
+      *nk_fixed = c->gcache[q].nk;
+      return c->gcache[q].exec;
+    }
+  cudaStream_t s = c->stream;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaGraph_t g = nullptr, tmp = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  cudaGraphNode_t cond = nullptr;
+  cudaGraphNode_t leaves[16];
+  size_t nleaves = 0;
+  const long n0 = c->nlaunch;
+  long n_body = 0;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+            cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, mode) == cudaSuccess;
+  if (ok) {
+    graph_prologue(c, p, h);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    ok = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
+         cs == cudaStreamCaptureStatusActive && nd >= 1 && nd <= 16;
+    if (ok)
+      for (size_t q = 0; q < nd; ++q) leaves[q] = deps[q];
+    nleaves = nd;
+    if (cudaStreamEndCapture(s, &tmp) != cudaSuccess) ok = false;
+  }
+  if (ok) {
+    // zeroed storage: the parameter union has no default constructor
+    alignas(cudaGraphNodeParams) unsigned char prm_raw[sizeof(cudaGraphNodeParams)];
+    memset(prm_raw, 0, sizeof(prm_raw));
+    cudaGraphNodeParams& prm = *reinterpret_cast<cudaGraphNodeParams*>(prm_raw);
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    ok = cudaGraphAddNode(&cond, g, leaves, nullptr, nleaves, &prm) == cudaSuccess;
+    if (ok) {
+      cudaGraph_t body = prm.conditional.phGraph_out[0];
+      ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, mode) == cudaSuccess;
+      if (ok) {
+        const long nb0 = c->nlaunch;
+        graph_body(c, p, h);
+        n_body = c->nlaunch - nb0;
+        if (cudaStreamEndCapture(s, &tmp) != cudaSuccess) ok = false;
+      }
+    }
+  }
+  if (ok) {
+    ok = cudaStreamBeginCaptureToGraph(s, g, &cond, nullptr, 1, mode) == cudaSuccess;
+    if (ok) {
+      graph_epilogue(c, p);
+      if (cudaStreamEndCapture(s, &tmp) != cudaSuccess) ok = false;
+    }
+  }
+  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  const long n_fixed = c->nlaunch - n0 - n_body;
+  c->nlaunch = n0;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(s, &tmp);
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();
+    c->graphs_ok = 0;
+    return nullptr;
+  }
+  auto& slot = c->gcache[c->gnext];
+  if (slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot.p = p;
+  slot.exec = exec;
+  slot.nk = n_fixed;
+  c->nk_body = n_body;
+  c->gnext = (c->gnext + 1) % 8;
+  *nk_fixed = n_fixed;
+  return exec;
+}
+
+// The pressure solve of a stage (record slot 0..2) or of fvm_poisson_solve
+// (slot 3), with beta0 already formed from alpha.  On the graph path the
+// cycles, the residual and the status stay on the device (record `slot`
+// and the sticky status) and *dev_side is set; otherwise the host loop
+// fills cyc, rel and returns the status.
+fvm_status solve(fvm_ctx* c, const void* alpha, double* p, int slot, int* cyc, double* rel,
+                 bool want_rel, bool* dev_side) {
+  *dev_side = false;
+  if (c->graphs_ok && !c->prof) {
+    long nk = 0;
+    cudaGraphExec_t exec = solve_graph(c, p, &nk);
+    if (exec) {
+      if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) return cuda_check(c, "solve graph launch");
+      c->nlaunch += nk;
+      TIMED(c, FVM_K_MISC, 1, launch_ctl_store(c->ctl, c->rec + slot, c->sticky, c->stream));
+      *dev_side = true;
+      *cyc = 0;
+      *rel = 0.0;
+      return FVM_OK;
+    }
+  }
+  if (c->mixed) return solve_mixed(c, (const float*)alpha, p, c->b, cyc, rel, want_rel);
+  return solve_f64(c, p, c->b, cyc, rel, want_rel);
+}
+
+// status of a device-side record, as the host loop would have returned it
+fvm_status record_status(fvm_ctx* c, const SolveCtl& r) {
+  if (r.status == FVM_EUNSTABLE)
+    return set_err(c, FVM_EUNSTABLE, "non-finite projection right-hand side or residual");
+  if (r.status == FVM_ENOCONV)
     return set_err(c, FVM_ENOCONV, "pressure solve reached mg_max_cycles above mg_rtol");
   return FVM_OK;
 }
@@ -615,7 +763,8 @@ Fields<R> fields_of(void* const* a) {
 // one forward-Euler stage E(X) and Y = a Sn + b E(X)
 template <typename R>
 fvm_status stage(fvm_ctx* c, Fields<R> X, Fields<R> Sn, Fields<R> Y, double* p, double ca,
-                 double cb, double xc, int* cyc, double* rel, bool want_rel) {
+                 double cb, double xc, int slot, int* cyc, double* rel, bool want_rel,
+                 bool* dev_side) {
   cudaStream_t s = c->stream;
   const Geo& g = c->g;
   R* M[3] = {(R*)c->M[0], (R*)c->M[1], (R*)c->M[2]};
@@ -633,13 +782,13 @@ fvm_status stage(fvm_ctx* c, Fields<R> X, Fields<R> Sn, Fields<R> Y, double* p, 
   if (c->mixed) {
     float* be[3] = {(float*)c->beta0[0], (float*)c->beta0[1], (float*)c->beta0[2]};
     TIMED(c, FVM_K_BETA, 1, launch_beta<R, float>(g, c->ph, (const R*)X.alpha, be[0], be[1], be[2], s));
-    st = solve_mixed(c, (const float*)X.alpha, p, c->b, cyc, rel, want_rel);
+    st = solve(c, X.alpha, p, slot, cyc, rel, want_rel, dev_side);
     if (st && st != FVM_ENOCONV) return st;
     TIMED(c, FVM_K_CORRECT, 1, launch_correct<R, float>(g, Sn, Y, us, p, be, c->dt_dev, ca, cb, s));
   } else {
     double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};
     TIMED(c, FVM_K_BETA, 1, launch_beta<R, double>(g, c->ph, (const R*)X.alpha, be[0], be[1], be[2], s));
-    st = solve_f64(c, p, c->b, cyc, rel, want_rel);
+    st = solve(c, X.alpha, p, slot, cyc, rel, want_rel, dev_side);
     if (st && st != FVM_ENOCONV) return st;
     TIMED(c, FVM_K_CORRECT, 1, launch_correct<R, double>(g, Sn, Y, us, p, be, c->dt_dev, ca, cb, s));
   }
@@ -669,12 +818,13 @@ fvm_status step_impl(fvm_ctx* c, fvm_state* st, long step_index, double dt_in,
   Fields<R> Ys[3] = {A, B, Sn};
   int cyc[3] = {0, 0, 0};
   double rel[3] = {0, 0, 0};
+  bool dev[3] = {false, false, false};
   fvm_status worst = FVM_OK;
   const bool want_rel = info != nullptr;
   for (int q = 0; q < 3; ++q) {
     double xc = c->prm.q_x0 + c->prm.q_speed * c->prm.h * ((double)step_index + RK[q][2]);
-    fvm_status r = stage<R>(c, Xs[q], Sn, Ys[q], st->p, RK[q][0], RK[q][1], xc, &cyc[q],
-                            &rel[q], want_rel);
+    fvm_status r = stage<R>(c, Xs[q], Sn, Ys[q], st->p, RK[q][0], RK[q][1], xc, q, &cyc[q],
+                            &rel[q], want_rel, &dev[q]);
     if (r == FVM_ENOCONV) worst = r;
     else if (r) return r;
   }
@@ -692,8 +842,20 @@ fvm_status step_impl(fvm_ctx* c, fvm_state* st, long step_index, double dt_in,
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->flags, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&dt, c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&lim, c->lim_dev, sizeof(int), cudaMemcpyDeviceToHost, s);
+    SolveCtl recs[3];
+    const bool any_dev = dev[0] || dev[1] || dev[2];
+    if (e == cudaSuccess && any_dev)
+      e = cudaMemcpyAsync(recs, c->rec, sizeof(recs), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_err(c, FVM_ECUDA, cudaGetErrorString(e));
+    for (int q = 0; q < 3; ++q) {
+      if (!dev[q]) continue;
+      cyc[q] = recs[q].iters;
+      rel[q] = recs[q].rel;
+      fvm_status r = record_status(c, recs[q]);
+      if (r == FVM_EUNSTABLE) return r;
+      if (r == FVM_ENOCONV) worst = r;
+    }
     double mdiv;
     memcpy(&mdiv, &mb, sizeof(double));
     double h3 = c->prm.h * c->prm.h * c->prm.h;
@@ -785,6 +947,12 @@ fvm_status fvm_create(const fvm_params* prm, void* workspace, size_t bytes, void
     }
   }
   c->graphs_ok = 1;
+  if (cudaMemsetAsync(c->ctl, 0, (1 + kRecords) * sizeof(SolveCtl) + sizeof(int) +
+                                     sizeof(unsigned long long), c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return FVM_ECUDA;
+  }
   snprintf(c->err, sizeof(c->err), "ok");
   *out = c;
   return FVM_OK;
@@ -792,7 +960,7 @@ fvm_status fvm_create(const fvm_params* prm, void* workspace, size_t bytes, void
 
 fvm_status fvm_destroy(fvm_ctx* ctx) {
   if (!ctx) return FVM_EINVAL;
-  for (int q = 0; q < 6; ++q)
+  for (int q = 0; q < 8; ++q)
     if (ctx->gcache[q].exec) cudaGraphExecDestroy(ctx->gcache[q].exec);
   if (ctx->prof_ev) {
     for (int q = 0; q < 2 * kProfSlots; ++q) cudaEventDestroy(ctx->prof_ev[q]);
@@ -827,8 +995,31 @@ fvm_status fvm_profile(fvm_ctx* ctx, int on) {
 
 fvm_status fvm_launch_count(fvm_ctx* ctx, int reset, long* count) {
   if (!ctx || !count) return FVM_EINVAL;
-  *count = ctx->nlaunch;
-  if (reset) ctx->nlaunch = 0;
+  // kernels of the device-side solve loops: cycles run so far times the
+  // kernels of one cycle (read after the stream has drained)
+  unsigned long long runs = 0;
+  cudaError_t e = cudaMemcpyAsync(&runs, ctx->runs, sizeof(runs), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return set_err(ctx, FVM_ECUDA, cudaGetErrorString(e));
+  *count = ctx->nlaunch + (long)(runs - ctx->runs_base) * ctx->nk_body;
+  if (reset) {
+    ctx->nlaunch = 0;
+    ctx->runs_base = runs;
+  }
+  return FVM_OK;
+}
+
+fvm_status fvm_sync(fvm_ctx* ctx) {
+  if (!ctx) return FVM_EINVAL;
+  int sticky = 0;
+  cudaError_t e = cudaMemcpyAsync(&sticky, ctx->sticky, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sticky, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return set_err(ctx, FVM_ECUDA, cudaGetErrorString(e));
+  if (sticky == FVM_EUNSTABLE)
+    return set_err(ctx, FVM_EUNSTABLE, "a pressure solve met a non-finite norm");
+  if (sticky == FVM_ENOCONV)
+    return set_err(ctx, FVM_ENOCONV, "a pressure solve reached mg_max_cycles above mg_rtol");
   return FVM_OK;
 }
 
@@ -865,14 +1056,23 @@ fvm_status fvm_poisson_solve(fvm_ctx* ctx, const void* alpha, const double* rhs,
   int cyc = 0;
   double rel = 0.0;
   fvm_status st;
+  bool dev_side = false;
   if (ctx->mixed) {
     float* be[3] = {(float*)ctx->beta0[0], (float*)ctx->beta0[1], (float*)ctx->beta0[2]};
     TIMED(ctx, FVM_K_BETA, 1, launch_beta<float, float>(g, ctx->ph, (const float*)alpha, be[0], be[1], be[2], s));
-    st = solve_mixed(ctx, (const float*)alpha, p, ctx->b, &cyc, &rel, info != nullptr);
   } else {
     double* be[3] = {(double*)ctx->beta0[0], (double*)ctx->beta0[1], (double*)ctx->beta0[2]};
     TIMED(ctx, FVM_K_BETA, 1, launch_beta<double, double>(g, ctx->ph, (const double*)alpha, be[0], be[1], be[2], s));
-    st = solve_f64(ctx, p, ctx->b, &cyc, &rel, info != nullptr);
+  }
+  st = solve(ctx, alpha, p, 3, &cyc, &rel, info != nullptr, &dev_side);
+  if (dev_side && info) {
+    SolveCtl r;
+    e = cudaMemcpyAsync(&r, ctx->rec + 3, sizeof(r), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_err(ctx, FVM_ECUDA, cudaGetErrorString(e));
+    cyc = r.iters;
+    rel = r.rel;
+    st = record_status(ctx, r);
   }
   if (info) {
     memset(info, 0, sizeof(*info));
@@ -1054,9 +1254,13 @@ fvm_status step_adjoint_impl(fvm_ctx* c, const fvm_state* st_n, long step_index,
   int cyc = 0;
   double rel = 0.0;
   fvm_status worst = FVM_OK;
+  bool recomputed_on_device = false;
   for (int q = 0; q < 2; ++q) {
+    bool dev_side = false;
     fvm_status r = stage<double>(c, q == 0 ? Sn : A, Sn, q == 0 ? A : B, c->apf, kRK[q][0],
-                                 kRK[q][1], source_x(c, step_index, q), &cyc, &rel, false);
+                                 kRK[q][1], source_x(c, step_index, q), q, &cyc, &rel, false,
+                                 &dev_side);
+    recomputed_on_device = recomputed_on_device || dev_side;
     if (r == FVM_ENOCONV) worst = r;
     else if (r) return r;
   }
@@ -1096,9 +1300,18 @@ fvm_status step_adjoint_impl(fvm_ctx* c, const fvm_state* st_n, long step_index,
   }
   TIMED(c, FVM_K_ADJOINT, 1, launch_zero_wall_faces(c->g, out, s));
   double th[2];
+  SolveCtl recs[2];
   ce = cudaMemcpyAsync(th, c->scal + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess && recomputed_on_device)
+    ce = cudaMemcpyAsync(recs, c->rec, sizeof(recs), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) return set_err(c, FVM_ECUDA, cudaGetErrorString(ce));
+  if (recomputed_on_device)
+    for (int q = 0; q < 2; ++q) {
+      fvm_status r = record_status(c, recs[q]);
+      if (r == FVM_EUNSTABLE) return r;
+      if (r == FVM_ENOCONV) worst = r;
+    }
   dtheta[0] += th[0];
   dtheta[1] += th[1];
   fvm_status e = cuda_check(c, "step adjoint");

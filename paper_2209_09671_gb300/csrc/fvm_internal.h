@@ -155,4 +155,26 @@ void launch_residual64(const Geo& g, const double* p, const double* b, float* co
                        float* r32, double* partial, double* out, cudaStream_t s);
 void launch_add_correction(long long n, double* p, const float* e, cudaStream_t s);
 
+// ----- device-side control of the pressure solve (fvm_mg.cu) -----------------
+// The stopping test of a solve runs on the device, inside a CUDA graph with
+// a conditional WHILE node: after every cycle (refinement) the controller
+// kernel forms ||b - L p|| / ||b|| from the two reduction slots and sets the
+// node's condition, so the host never waits for a residual.
+struct SolveCtl {
+  int iters;      // cycles (F64) or refinements (MIXED) done
+  int status;     // 0, FVM_ENOCONV or FVM_EUNSTABLE
+  int zero;       // 1: ||b|| = 0, the solution is set to 0
+  int pad;
+  double rel;     // last relative residual
+};
+void launch_ctl_reset(SolveCtl* ctl, cudaStream_t s);
+// bn2 = ||b||^2 and r2 = ||b - L p||^2 (device); fixed > 0: exactly `fixed`
+// cycles; runs_total counts the cycles of every solve (launch bookkeeping)
+void launch_ctl_step(cudaGraphConditionalHandle h, SolveCtl* ctl, const double* bn2,
+                     const double* r2, double rtol, int maxit, int fixed,
+                     unsigned long long* runs_total, cudaStream_t s);
+void launch_zero_if_rhs_zero(const SolveCtl* ctl, double* p, long long n, cudaStream_t s);
+// copy the controller into a per-stage record and raise the sticky status
+void launch_ctl_store(const SolveCtl* ctl, SolveCtl* rec, int* sticky, cudaStream_t s);
+
 }  // namespace fvm

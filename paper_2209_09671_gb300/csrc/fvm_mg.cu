@@ -513,6 +513,76 @@ void launch_add_correction(long long n, double* p, const float* e, cudaStream_t 
   k_add_correction<<<grid1d(n, 256), 256, 0, s>>>(n, p, e);
 }
 
+// ---------------------------------------------------------------------------
+// device-side control of the pressure solve (one thread each)
+__global__ void k_ctl_reset(SolveCtl* ctl) {
+  ctl->iters = 0;
+  ctl->status = 0;
+  ctl->zero = 0;
+  ctl->rel = 0.0;
+}
+
+void launch_ctl_reset(SolveCtl* ctl, cudaStream_t s) { k_ctl_reset<<<1, 1, 0, s>>>(ctl); }
+
+// the stopping rule of the host loop, on the device: stop on a non-finite
+// norm (EUNSTABLE), a zero right-hand side, after `fixed` cycles, at
+// rel <= rtol, or at maxit cycles above rtol (ENOCONV)
+__global__ void k_ctl_step(cudaGraphConditionalHandle h, SolveCtl* ctl, const double* bn2p,
+                           const double* r2p, double rtol, int maxit, int fixed,
+                           unsigned long long* runs_total) {
+  const double bn2 = *bn2p;
+  unsigned go = 0;
+  if (!isfinite(bn2)) {
+    ctl->status = FVM_EUNSTABLE;
+  } else if (bn2 == 0.0) {
+    ctl->zero = 1;
+    ctl->rel = 0.0;
+  } else {
+    const double rel = sqrt(*r2p) / sqrt(bn2);
+    ctl->rel = rel;
+    if (!isfinite(rel)) {
+      ctl->status = FVM_EUNSTABLE;
+    } else if (fixed > 0) {
+      go = ctl->iters < fixed;
+    } else {
+      go = rel > rtol && ctl->iters < maxit;
+      if (!go && rel > rtol) ctl->status = FVM_ENOCONV;
+    }
+  }
+  if (go) {
+    ctl->iters += 1;
+    *runs_total += 1ull;
+  }
+  cudaGraphSetConditional(h, go);
+}
+
+void launch_ctl_step(cudaGraphConditionalHandle h, SolveCtl* ctl, const double* bn2,
+                     const double* r2, double rtol, int maxit, int fixed,
+                     unsigned long long* runs_total, cudaStream_t s) {
+  k_ctl_step<<<1, 1, 0, s>>>(h, ctl, bn2, r2, rtol, maxit, fixed, runs_total);
+}
+
+__global__ void k_zero_if_rhs_zero(const SolveCtl* __restrict__ ctl, double* __restrict__ p,
+                                   long long n) {
+  if (!ctl->zero) return;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    p[c] = 0.0;
+}
+
+void launch_zero_if_rhs_zero(const SolveCtl* ctl, double* p, long long n, cudaStream_t s) {
+  k_zero_if_rhs_zero<<<kRedBlocks, 256, 0, s>>>(ctl, p, n);
+}
+
+__global__ void k_ctl_store(const SolveCtl* ctl, SolveCtl* rec, int* sticky) {
+  *rec = *ctl;
+  if (ctl->status) atomicMax(sticky, ctl->status);
+}
+
+void launch_ctl_store(const SolveCtl* ctl, SolveCtl* rec, int* sticky, cudaStream_t s) {
+  k_ctl_store<<<1, 1, 0, s>>>(ctl, rec, sticky);
+}
+
 #define FVM_MG_INST(T)                                                                       \
   template void launch_sum_field<T>(const T*, long long, bool, double*, double*,             \
                                     cudaStream_t);                                           \

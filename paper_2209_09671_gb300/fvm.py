@@ -66,7 +66,7 @@ class fvm_step_info(ctypes.Structure):
 EXPORTS = ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step", "fvm_poisson_solve",
            "fvm_step_adjoint", "fvm_status_string", "fvm_last_error", "fvm_version",
            "fvm_profile", "fvm_profile_read", "fvm_launch_count", "fvm_poisson_solve_noalloc",
-           "fvm_stage_predict", "fvm_fma_peak")
+           "fvm_stage_predict", "fvm_fma_peak", "fvm_sync")
 
 KERNEL_CLASSES = ("smooth", "interface", "scalars", "momentum", "div_rhs", "beta", "gs_fine",
                   "gs_coarse", "restrict_fine", "restrict_coarse", "prolong_fine",
@@ -110,13 +110,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_void_p]
     lib.fvm_poisson_solve_noalloc.argtypes = [P(fvm_params), ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, P(fvm_step_info)]
+    lib.fvm_sync.argtypes = [ctypes.c_void_p]
     lib.fvm_fma_peak.argtypes = [ctypes.c_int, ctypes.c_void_p, P(ctypes.c_double),
                                  P(ctypes.c_double)]
     lib.fvm_profile_read.argtypes = [ctypes.c_void_p, ctypes.c_int, P(ctypes.c_long),
                                      P(ctypes.c_double)]
     for name in ("fvm_workspace_size", "fvm_create", "fvm_destroy", "fvm_step",
                  "fvm_poisson_solve", "fvm_step_adjoint", "fvm_profile", "fvm_profile_read", "fvm_launch_count",
-                 "fvm_poisson_solve_noalloc", "fvm_stage_predict", "fvm_fma_peak"):
+                 "fvm_poisson_solve_noalloc", "fvm_stage_predict", "fvm_fma_peak", "fvm_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -266,6 +267,14 @@ class Solver:
                                        ctypes.byref(self._state(lam_n, need_p=False)), dth)
         self._check(rc, "fvm_step_adjoint")
         return lam_n, [dth[0], dth[1]]
+
+    def fvm_sync(self, raise_on_error: bool = True) -> int:
+        """Wait for the solver's stream; the worst status of the device-side
+        pressure solves since the last call (raises unless FVM_OK)."""
+        rc = self.lib.fvm_sync(self.ctx)
+        if raise_on_error:
+            self._check(rc, "fvm_sync")
+        return rc
 
     def fvm_profile(self, on: bool):
         self._check(self.lib.fvm_profile(self.ctx, 1 if on else 0), "fvm_profile")

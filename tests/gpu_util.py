@@ -20,12 +20,18 @@ def need_gpu():
     return P
 
 
-def gpu_step(P, prm, state, step_index=0, dt=0.0, nsteps=1):
-    solver = P.Solver(prm)
-    dev = P.to_device(state, prm.precision == cases.MIXED)
-    infos = []
-    for n in range(nsteps):
-        infos.append(solver.fvm_step(dev, step_index + n, dt))
+def gpu_step(P, prm, state, step_index=0, dt=0.0, nsteps=1, stream=True):
+    """Steps through the C ABI.  On a stream of its own (the default) every
+    pressure solve runs as a CUDA graph with its stopping test on the
+    device; stream=False uses the legacy default stream, which cannot be
+    captured, so the solves run as eager launches with the host loop."""
+    st = torch.cuda.Stream() if stream else torch.cuda.current_stream()
+    with torch.cuda.stream(st):
+        solver = P.Solver(prm, stream=st)
+        dev = P.to_device(state, prm.precision == cases.MIXED)
+        infos = []
+        for n in range(nsteps):
+            infos.append(solver.fvm_step(dev, step_index + n, dt))
     torch.cuda.synchronize()
     host = {k: dev[k].double().cpu().numpy() for k in FIELDS}
     solver.close()
