@@ -114,6 +114,12 @@ class Params:
     precision: int = F64
     mx_inner_cycles: int = 2
     adjoint: int = 0
+    concentration: int = 0                              # 1: transport c, sigma(c, T)
+    dsigma_dc: float = 0.0                              # sigma += dsigma_dc (c - c0)
+    c0: float = 0.0
+    diff_c: tuple = (0.0, 0.0)                          # diffusivity of c per phase
+    weno_scale_c: float = 1.0                           # WENO5 eps scale of c
+    alpha_scheme: int = 0                               # 0 WENO5, 1 bounded (FCT blend)
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
@@ -128,7 +134,8 @@ class Params:
 
 
 def zero_state(p: Params) -> dict:
-    s = {k: np.zeros(p.shape) for k in ("u", "v", "w", "alpha", "T", "p")}
+    keys = ("u", "v", "w", "alpha", "T", "p") + (("c",) if p.concentration else ())
+    s = {k: np.zeros(p.shape) for k in keys}
     return s
 
 
@@ -338,6 +345,15 @@ def random_smooth_state(p: Params, seed: int = SEED, amp_u: float = 1.0,
                 * np.cos(2 * math.pi * ky * y / L[1] + 6.283 * mrow[5]) \
                 * np.cos(2 * math.pi * kz * z / L[2] + 6.283 * mrow[6])
         s[name][:] = a * f
+    if p.concentration:
+        r = uniform(seed + 11, (modes, 7), 0.0, 1.0)
+        f = np.zeros(p.shape)
+        for mrow in r:
+            kx, ky, kz = (1 + int(3 * mrow[0]), 1 + int(3 * mrow[1]), 1 + int(3 * mrow[2]))
+            f = f + (2 * mrow[3] - 1) * np.cos(2 * math.pi * kx * x / L[0] + 6.283 * mrow[4]) \
+                * np.cos(2 * math.pi * ky * y / L[1] + 6.283 * mrow[5]) \
+                * np.cos(2 * math.pi * kz * z / L[2] + 6.283 * mrow[6])
+        s["c"][:] = 0.5 + 0.25 * f
     if p.nz == 1:
         s["w"][:] = 0.0
     if drop:

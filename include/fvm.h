@@ -96,13 +96,29 @@ typedef struct {
   int mx_inner_cycles;                     /* float V-cycles per double refinement */
   int adjoint;                             /* 1: also reserve the buffers of      */
                                            /* fvm_step_adjoint (F64 only)        */
+  /* solutal Marangoni (Eq. 5, second term): a transported concentration c,
+   * advected by WENO5 like T and diffused with the harmonic face mean of the
+   * mixture diffusivity (no flux through walls); sigma(c, T) = sigma0 +
+   * dsigma_dT (T - T0) + dsigma_dc (c - c0) is formed per cell and
+   * differentiated as a field (Sec. IV).  concentration = 0 leaves c out. */
+  int concentration;                       /* 1: fvm_state.c is transported      */
+  double dsigma_dc, c0;
+  double diff_c[2];                        /* diffusivity of c per phase (>= 0)  */
+  double weno_scale_c;                     /* WENO5 eps = weno_eps*scale_c^2     */
+  /* phase-fraction fluxes (Eq. 1): 0 WENO5; 1 bounded, the flux-corrected
+   * blend (Zalesak 1979) of the first-order upwind and the WENO5 flux that
+   * keeps every stage's alpha within [0, 1] (the paper's Sec. V-A mixes
+   * first-order bounded and high-order WENO schemes); not with adjoint = 1 */
+  int alpha_scheme;
 } fvm_params;
 
-/* Caller-owned device fields of one state. u, v, w, alpha, T: double (F64) or
- * float (MIXED); p: double in both forms. */
+/* Caller-owned device fields of one state. u, v, w, alpha, T (and c): double
+ * (F64) or float (MIXED); p: double in both forms.  c is the concentration
+ * when fvm_params.concentration = 1 (required then, ignored otherwise). */
 typedef struct {
   void *u, *v, *w, *alpha, *T;
   double *p;
+  void *c;
 } fvm_state;
 
 typedef struct {

@@ -15,8 +15,9 @@ check it against the paper line by line:
 * Sec. III, Eq. 2-4 -- capillary stress split into the normal CSF force
   -sigma kappa n delta_s and the tangential Marangoni force
   delta_s (I - n n) grad sigma (``interface_forces``).
-* Sec. III, Eq. 5 and Sec. IV -- sigma evaluated cell-wise from T and
-  differentiated as a field (``sigma_of_T``, central differences of sigma).
+* Sec. III, Eq. 5 and Sec. IV -- sigma evaluated cell-wise from T (and from
+  a transported concentration c, the solutal term of Eq. 5) and
+  differentiated as a field (``sigma_field``, central differences of sigma).
 * Sec. III, delta_s = |grad alpha| and n = grad alpha / delta_s.
 * Sec. III -- incompressible Navier-Stokes and energy equations, which the
   paper names but does not write out: momentum predictor with WENO5
@@ -276,6 +277,22 @@ def sigma_of_T(T, prm):
     return prm.sigma0 + prm.dsigma_dT * (T - prm.T0)
 
 
+def has_concentration(prm):
+    return int(getattr(prm, "concentration", 0)) == 1
+
+
+def sigma_field(T, c, prm):
+    """sigma(c, T) as a cell field (Eq. 5 with the chain rule of its
+    gradient; Sec. IV: sigma is formed locally from every field it depends
+    on and then differentiated as a field): sigma0 + (dsigma/dT)(T - T0)
+    + (dsigma/dc)(c - c0), the concentration term only when a transported
+    concentration is present."""
+    s = sigma_of_T(T, prm)
+    if c is not None:
+        s = s + prm.dsigma_dc * (c - prm.c0)
+    return s
+
+
 # ==========================================================================
 # WENO5-JS reconstruction (Jiang & Shu 1996), Sec. IV "high order WENO"
 # ==========================================================================
@@ -419,15 +436,80 @@ def scalar_rhs(phiP, velP, grid, eps):
     return R
 
 
+def bounded_alpha_rhs(Ap, velP, grid, eps, dt):
+    """-div(u alpha) with fluxes kept between the first-order upwind flux and
+    the WENO5 flux so that the forward-Euler stage keeps alpha within [0, 1]
+    (the bounded option of the transport scheme; the paper's Sec. V-A mixes
+    first-order bounded and high-order WENO divergence schemes).  The blend
+    is flux-corrected transport (Zalesak, J. Comput. Phys. 31, 1979) with the
+    global bounds 0 and 1:
+
+    F_L = U alpha_upwind, A = F_WENO - F_L (antidiffusive part),
+    alpha_td = alpha - dt div F_L (bounded for a divergence-free U at the
+    CFL limit), per cell P+ / P- = sum of antidiffusive fluxes into / out of
+    it, Q+ = (1 - alpha_td) h / dt, Q- = alpha_td h / dt,
+    R+- = clamp(Q+- / P+-, 0, 1) (0 where P vanishes); a face with A > 0
+    (from its low cell L to its high cell R) takes theta = min(R+_R, R-_L),
+    with A < 0 theta = min(R+_L, R-_R); the flux is F_L + theta A."""
+    h = grid.h
+    n = grid.shape
+    FL, AA = [], []
+    for d in range(3):
+        FLd, Ad = [], []
+        for s in (0, 1):
+            U = Sd(velP[d], grid, (d, s))
+            vals = [Sd(Ap, grid, (d, s + k)) for k in (-3, -2, -1, 0, 1, 2)]
+            fh = upwind_flux(U, vals, eps)
+            fl = torch.where(U >= 0.0, U * vals[2], U * vals[3])
+            FLd.append(fl)
+            Ad.append(fh - fl)
+        FL.append(FLd)
+        AA.append(Ad)
+    alpha = S(Ap, grid)
+    div_low = torch.zeros(n, dtype=DT)
+    Pp = torch.zeros(n, dtype=DT)
+    Pm = torch.zeros(n, dtype=DT)
+    for d in range(3):
+        div_low = div_low + (FL[d][1] - FL[d][0]) / h
+        a_lo, a_hi = AA[d][0], AA[d][1]
+        Pp = Pp + torch.clamp(a_lo, min=0.0) + torch.clamp(-a_hi, min=0.0)
+        Pm = Pm + torch.clamp(-a_lo, min=0.0) + torch.clamp(a_hi, min=0.0)
+    a_td = alpha - dt * div_low
+    Qp = (1.0 - a_td) * h / dt
+    Qm = a_td * h / dt
+
+    def ratio(Q, P):
+        pos = P > 0.0
+        return torch.where(pos, torch.clamp(Q / torch.where(pos, P, 1.0), 0.0, 1.0), 0.0)
+
+    Rp, Rm = ratio(Qp, Pp), ratio(Qm, Pm)
+    RpP, RmP = pad_scalar(Rp, grid, 1.0), pad_scalar(Rm, grid, 1.0)
+    out = torch.zeros(n, dtype=DT)
+    for d in range(3):
+        F = []
+        for s in (0, 1):
+            a = AA[d][s]
+            # the face's low cell L = c + (s-1) e_d, high cell R = c + s e_d
+            rpL, rmL = Sd(RpP, grid, (d, s - 1)), Sd(RmP, grid, (d, s - 1))
+            rpR, rmR = Sd(RpP, grid, (d, s)), Sd(RmP, grid, (d, s))
+            theta = torch.where(a > 0.0, torch.minimum(rpR, rmL),
+                                torch.where(a < 0.0, torch.minimum(rpL, rmR), torch.ones_like(a)))
+            F.append(FL[d][s] + theta * a)
+        out = out - (F[1] - F[0]) / h
+    return out
+
+
 def diffusion_rhs(TP, lamP, grid):
-    """div(lambda grad T) with the harmonic mean of lambda on each face."""
+    """div(lambda grad T) with the harmonic mean of lambda on each face (0 on
+    a face where lambda vanishes on both sides)."""
     h = grid.h
     R = torch.zeros(grid.shape, dtype=DT)
     for d in range(3):
         D = []
         for s in (0, 1):
             lL, lR = Sd(lamP, grid, (d, s - 1)), Sd(lamP, grid, (d, s))
-            lf = 2.0 * lL * lR / (lL + lR)
+            den = lL + lR
+            lf = torch.where(den > 0.0, 2.0 * lL * lR / torch.where(den > 0.0, den, 1.0), 0.0)
             D.append(lf * (Sd(TP, grid, (d, s)) - Sd(TP, grid, (d, s - 1))) / h)
         R = R + (D[1] - D[0]) / h
     return R
@@ -498,7 +580,7 @@ def _zero_wall_face(a, d):
     return a
 
 
-def interface_forces(alpha, alpha_s, T, prm, grid):
+def interface_forces(alpha, alpha_s, T, prm, grid, c=None):
     """Face forces from Eq. 4 in balanced-force form, per direction d:
 
     f_n = -sigma_f kappa_f (alpha_R - alpha_L)/h  (the normal term
@@ -513,7 +595,8 @@ def interface_forces(alpha, alpha_s, T, prm, grid):
     Ap = pad_scalar(alpha, grid, 1.0)
     Asp = pad_scalar(alpha_s, grid, 1.0)
     TP = pad_temperature(T, prm, grid)
-    sigP = sigma_of_T(TP, prm)
+    cP = pad_scalar(c, grid, 1.0) if c is not None else None
+    sigP = sigma_field(TP, cP, prm)
     M, gnorm = marangoni_vector(Ap, Asp, sigP, grid)
     MP = [pad_scalar(M[d], grid, 1.0) for d in range(3)]
     out = []
@@ -772,13 +855,18 @@ def time_step_limit(state, prm, grid):
     """dt = min(CFL, capillary, viscous, thermal, dt_max) from max-reductions:
     C_u h / (max|u|+max|v|+max|w|), C_sigma sqrt((rho0+rho1) h^3 / (4 pi max|sigma|)),
     C_nu h^2 / max(mu/rho), C_kappa h^2 / max(lambda/(rho c_p)).
+    With a transported concentration, max(mu/rho) is joined in the last limit
+    by max(D_c) and |sigma| is that of sigma(c, T).
     Returns (dt, index of the binding limit)."""
     h = grid.h
     umax = sum(state[k].abs().max().item() for k in ("u", "v", "w"))
     a = state["alpha"]
-    smax = sigma_of_T(state["T"], prm).abs().max().item()
+    c = state["c"] if has_concentration(prm) else None
+    smax = sigma_field(state["T"], c, prm).abs().max().item()
     numax = (mix(a, prm.mu) / mix(a, prm.rho)).max().item()
     kapmax = (mix(a, prm.lam) / rho_cp(a, prm)).max().item()
+    if c is not None:   # the concentration's diffusion shares the diffusive limit
+        kapmax = max(kapmax, mix(a, prm.diff_c).max().item())
     lim = [math.inf] * 5
     if umax > 0.0:
         lim[0] = prm.cfl * h / umax
@@ -800,13 +888,17 @@ def predictor(X, prm, grid, dt, step_index, c_stage):
     alpha, T = X["alpha"], X["T"]
     vel = [X["u"], X["v"], X["w"]]
     velP = [pad_velocity(vel[d], grid, d) for d in range(3)]
+    c = X["c"] if has_concentration(prm) else None
     alpha_s = smooth_alpha(alpha, grid, prm.smooth_passes)
-    forces, kappa, gnorm = interface_forces(alpha, alpha_s, T, prm, grid)
+    forces, kappa, gnorm = interface_forces(alpha, alpha_s, T, prm, grid, c)
     Ap = pad_scalar(alpha, grid, 1.0)
     TP = pad_temperature(T, prm, grid)
     eps = [prm.weno_eps * s * s for s in prm.weno_scale]
     # phase fraction (Eq. 1) and temperature
-    R_alpha = scalar_rhs(Ap, velP, grid, eps[0])
+    if int(getattr(prm, "alpha_scheme", 0)) == 1:
+        R_alpha = bounded_alpha_rhs(Ap, velP, grid, eps[0], dt)
+    else:
+        R_alpha = scalar_rhs(Ap, velP, grid, eps[0])
     lamP = mix(Ap, prm.lam)
     rcp = rho_cp(alpha, prm)
     R_T = scalar_rhs(TP, velP, grid, eps[1]) + diffusion_rhs(TP, lamP, grid) / rcp
@@ -815,16 +907,27 @@ def predictor(X, prm, grid, dt, step_index, c_stage):
         R_T = R_T + q * gnorm / rcp
     props = {"muP": mix(Ap, prm.mu), "rhoP": mix(Ap, prm.rho)}
     ustar = [momentum_predictor(d, velP, prm, grid, dt, props, forces, eps[2]) for d in range(3)]
-    return {"alpha": alpha + dt * R_alpha, "T": T + dt * R_T, "ustar": ustar,
-            "alpha_s": alpha_s, "kappa": kappa}
+    out = {"alpha": alpha + dt * R_alpha, "T": T + dt * R_T, "ustar": ustar,
+           "alpha_s": alpha_s, "kappa": kappa}
+    if c is not None:
+        # a transported concentration (the solutal part of Eq. 5): WENO5
+        # advection like T and diffusion with the harmonic face mean of the
+        # mixture diffusivity, even (no-flux) at walls
+        cP = pad_scalar(c, grid, 1.0)
+        R_c = scalar_rhs(cP, velP, grid, prm.weno_eps * prm.weno_scale_c ** 2) + \
+            diffusion_rhs(cP, mix(Ap, prm.diff_c), grid)
+        out["c"] = c + dt * R_c
+    return out
 
 
 def substep(X, prm, grid, dt, step_index, c_stage, fixed_cycles=None):
     """E(X): forward-Euler predictor followed by the projection."""
     pr = predictor(X, prm, grid, dt, step_index, c_stage)
     vel, p, cycles, rel = projection(pr["ustar"], X["alpha"], X["p"], prm, grid, dt, fixed_cycles)
-    return {"u": vel[0], "v": vel[1], "w": vel[2], "alpha": pr["alpha"], "T": pr["T"], "p": p}, \
-        cycles, rel
+    E = {"u": vel[0], "v": vel[1], "w": vel[2], "alpha": pr["alpha"], "T": pr["T"], "p": p}
+    if "c" in pr:
+        E["c"] = pr["c"]
+    return E, cycles, rel
 
 
 RK3 = ((0.0, 1.0, 0.0), (0.75, 0.25, 1.0), (1.0 / 3.0, 2.0 / 3.0, 0.5))
@@ -855,18 +958,23 @@ def step(state, prm, step_index=0, dt=0.0, fixed_cycles=None):
         E, cyc, rel = substep(X, prm, grid, dt, step_index, c, fc)
         vcycles.append(cyc)
         rels.append(rel)
-        X = {k: a * Sn[k] + b * E[k] for k in ("u", "v", "w", "alpha", "T")}
+        X = {k: a * Sn[k] + b * E[k] for k in transported(prm)}
         X["p"] = E["p"]
     info = diagnostics(X, prm, grid, dt)
     info.update({"dt": dt, "dt_limiter": limiter, "vcycles": vcycles, "rel_residual": rels})
     return X, info
 
 
+def transported(prm):
+    """The fields the time integrator advances (the concentration when present)."""
+    return ("u", "v", "w", "alpha", "T") + (("c",) if has_concentration(prm) else ())
+
+
 def diagnostics(X, prm, grid, dt):
     """Volume sum alpha h^3, mass sum rho(alpha) h^3, max |D u| dt, NaN flag."""
     h3 = grid.h ** 3
     div = divergence([X["u"], X["v"], X["w"]], grid)
-    finite = all(torch.isfinite(X[k]).all().item() for k in ("u", "v", "w", "alpha", "T", "p"))
+    finite = all(torch.isfinite(X[k]).all().item() for k in transported(prm) + ("p",))
     return {"vol_sum": (X["alpha"].sum() * h3).item(),
             "mass_sum": (mix(X["alpha"], prm.rho).sum() * h3).item(),
             "max_div_dt": (div.abs().max() * dt).item(),

@@ -113,6 +113,14 @@ const char* check_params(const fvm_params* p) {
   if (p->q_power != 0.0 && !(p->q_radius > 0.0)) return "q_radius must be > 0";
   if (p->adjoint != 0 && p->adjoint != 1) return "adjoint must be 0 or 1";
   if (p->adjoint && p->precision != FVM_F64) return "the adjoint needs precision F64";
+  if (p->concentration != 0 && p->concentration != 1) return "concentration must be 0 or 1";
+  if (p->alpha_scheme != 0 && p->alpha_scheme != 1) return "alpha_scheme must be 0 or 1";
+  if (p->alpha_scheme == 1 && p->adjoint) return "the adjoint does not support the bounded scheme";
+  if (p->concentration) {
+    if (!(p->diff_c[0] >= 0.0) || !(p->diff_c[1] >= 0.0)) return "diff_c must be >= 0";
+    if (!(p->weno_scale_c != 0.0)) return "weno_scale_c must be nonzero";
+    if (p->adjoint) return "the adjoint does not support a concentration";
+  }
   return nullptr;
 }
 
@@ -129,8 +137,9 @@ struct fvm_ctx {
   char* ws;
   size_t ws_bytes;
   // stage buffers (working precision)
-  void* A[5];
-  void* B[5];
+  void* A[6];            // stage copies: u, v, w, alpha, T and the concentration
+  void* B[6];            // (null without one)
+  void* fct[2];          // limiter ratios R+, R- of the bounded alpha transport
   void* as;
   void* tmp;
   void* kappa;
@@ -237,9 +246,13 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
   bool mixed = p.precision == FVM_MIXED;
   size_t rs = mixed ? sizeof(float) : sizeof(double);
   size_t ms = rs;   // multigrid precision: double in F64, float (inner) in MIXED
-  size_t o_A[5], o_B[5], o_as, o_tmp, o_k, o_M[3], o_us[3], o_b, o_beta[3], o_e = 0, o_r = 0;
-  for (int q = 0; q < 5; ++q) o_A[q] = pl.take(N * rs);
-  for (int q = 0; q < 5; ++q) o_B[q] = pl.take(N * rs);
+  size_t o_A[6], o_B[6], o_as, o_tmp, o_k, o_M[3], o_us[3], o_b, o_beta[3], o_e = 0, o_r = 0;
+  const int nstage = p.concentration ? 6 : 5;
+  for (int q = 0; q < nstage; ++q) o_A[q] = pl.take(N * rs);
+  for (int q = 0; q < nstage; ++q) o_B[q] = pl.take(N * rs);
+  size_t o_fct[2] = {0, 0};
+  if (p.alpha_scheme == 1)
+    for (int q = 0; q < 2; ++q) o_fct[q] = pl.take(N * rs);
   o_as = pl.take(N * rs);
   o_tmp = pl.take(N * rs);
   o_k = pl.take(N * rs);
@@ -277,7 +290,11 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
   }
   if (c) {
     char* w = c->ws;
-    for (int q = 0; q < 5; ++q) { c->A[q] = w + o_A[q]; c->B[q] = w + o_B[q]; }
+    for (int q = 0; q < 6; ++q) {
+      c->A[q] = q < nstage ? w + o_A[q] : nullptr;
+      c->B[q] = q < nstage ? w + o_B[q] : nullptr;
+    }
+    for (int q = 0; q < 2; ++q) c->fct[q] = p.alpha_scheme == 1 ? w + o_fct[q] : nullptr;
     c->as = w + o_as;
     c->tmp = w + o_tmp;
     c->kappa = w + o_k;
@@ -757,6 +774,7 @@ Fields<R> fields_of(void* const* a) {
   f.u[2] = (R*)a[2];
   f.alpha = (R*)a[3];
   f.T = (R*)a[4];
+  f.c = (R*)a[5];
   return f;
 }
 
@@ -771,8 +789,13 @@ fvm_status stage(fvm_ctx* c, Fields<R> X, Fields<R> Sn, Fields<R> Y, double* p, 
   R* us[3] = {(R*)c->us[0], (R*)c->us[1], (R*)c->us[2]};
   // smoothed alpha, normals, curvature and Marangoni vector in one kernel
   TIMED(c, FVM_K_INTERFACE, 1, launch_interface<R>(g, c->ph, c->tb, c->prm.smooth_passes, X.alpha,
-                                                X.T, (R*)c->kappa, M[0], M[1], M[2], s));
-  TIMED(c, FVM_K_SCALARS, 1, launch_scalars<R>(g, c->ph, c->tb, X, Sn, Y, c->dt_dev, ca, cb, xc, s));
+                                                X.T, X.c, (R*)c->kappa, M[0], M[1], M[2], s));
+  if (c->fct[0])
+    TIMED(c, FVM_K_SCALARS, 1, launch_fct_ratios<R>(g, c->ph, X, c->dt_dev, (R*)c->fct[0], (R*)c->fct[1], s));
+  TIMED(c, FVM_K_SCALARS, 1, launch_scalars<R>(g, c->ph, c->tb, X, Sn, Y, c->dt_dev, ca, cb, xc,
+                                            (const R*)c->fct[0], (const R*)c->fct[1], s));
+  if (X.c)
+    TIMED(c, FVM_K_SCALARS, 1, launch_concentration<R>(g, c->ph, X, Sn, Y, c->dt_dev, ca, cb, s));
   TIMED(c, FVM_K_MOMENTUM, 1, launch_momentum<R>(g, c->ph, c->tb, X, (R*)c->kappa, M[0], M[1], M[2],
                                               us[0], us[1], us[2], c->dt_dev, s));
   TIMED(c, FVM_K_DIV_RHS, 1, launch_div_rhs<R>(g, us, c->dt_dev, c->b, c->partial, s));
@@ -800,7 +823,7 @@ template <typename R>
 fvm_status step_impl(fvm_ctx* c, fvm_state* st, long step_index, double dt_in,
                      fvm_step_info* info) {
   cudaStream_t s = c->stream;
-  void* sp[5] = {st->u, st->v, st->w, st->alpha, st->T};
+  void* sp[6] = {st->u, st->v, st->w, st->alpha, st->T, c->prm.concentration ? st->c : nullptr};
   Fields<R> Sn = fields_of<R>(sp);
   Fields<R> A = fields_of<R>(c->A);
   Fields<R> B = fields_of<R>(c->B);
@@ -930,6 +953,11 @@ fvm_status fvm_create(const fvm_params* prm, void* workspace, size_t bytes, void
   ph.L[0] = prm->nx * prm->h;
   ph.L[1] = prm->ny * prm->h;
   ph.L[2] = prm->nz * prm->h;
+  ph.dsdc = prm->concentration ? prm->dsigma_dc : 0.0;
+  ph.c0 = prm->c0;
+  ph.diff_c[0] = prm->diff_c[0];
+  ph.diff_c[1] = prm->diff_c[1];
+  ph.eps_c = prm->weno_eps * prm->weno_scale_c * prm->weno_scale_c;
   TBC& tb = c->tb;
   tb.axis = -1;
   for (int d = 0; d < 3; ++d) {
@@ -1036,6 +1064,8 @@ fvm_status fvm_step(fvm_ctx* ctx, fvm_state* st, long step_index, double dt, fvm
   if (!ctx) return FVM_EINVAL;
   if (!st || !st->u || !st->v || !st->w || !st->alpha || !st->T || !st->p)
     return set_err(ctx, FVM_EINVAL, "null state pointer");
+  if (ctx->prm.concentration && !st->c)
+    return set_err(ctx, FVM_EINVAL, "null concentration with concentration = 1");
   if (!(dt == dt)) return set_err(ctx, FVM_EINVAL, "dt is NaN");
   cudaGetLastError();
   if (ctx->mixed) return step_impl<float>(ctx, st, step_index, dt, info);
@@ -1092,7 +1122,7 @@ fvm_status predict_impl(fvm_ctx* c, const fvm_state* X_, long step_index, double
                         void* const* ustar, void* alpha_out, void* T_out) {
   cudaStream_t s = c->stream;
   const Geo& g = c->g;
-  void* xp[5] = {X_->u, X_->v, X_->w, X_->alpha, X_->T};
+  void* xp[6] = {X_->u, X_->v, X_->w, X_->alpha, X_->T, c->prm.concentration ? X_->c : nullptr};
   Fields<R> X = fields_of<R>(xp);
   Fields<R> Y = X;
   Y.alpha = (R*)alpha_out;
@@ -1101,8 +1131,12 @@ fvm_status predict_impl(fvm_ctx* c, const fvm_state* X_, long step_index, double
   const double xc = c->prm.q_x0 + c->prm.q_speed * c->prm.h * (double)step_index;
   R* M[3] = {(R*)c->M[0], (R*)c->M[1], (R*)c->M[2]};
   TIMED(c, FVM_K_INTERFACE, 1, launch_interface<R>(g, c->ph, c->tb, c->prm.smooth_passes, X.alpha,
-                                                X.T, (R*)c->kappa, M[0], M[1], M[2], s));
-  TIMED(c, FVM_K_SCALARS, 1, launch_scalars<R>(g, c->ph, c->tb, X, X, Y, c->dt_dev, 0.0, 1.0, xc, s));
+                                                X.T, X.c, (R*)c->kappa, M[0], M[1], M[2], s));
+  Y.c = nullptr;   // the concentration update is not part of the predictor's outputs
+  if (c->fct[0])
+    TIMED(c, FVM_K_SCALARS, 1, launch_fct_ratios<R>(g, c->ph, X, c->dt_dev, (R*)c->fct[0], (R*)c->fct[1], s));
+  TIMED(c, FVM_K_SCALARS, 1, launch_scalars<R>(g, c->ph, c->tb, X, X, Y, c->dt_dev, 0.0, 1.0, xc,
+                                            (const R*)c->fct[0], (const R*)c->fct[1], s));
   TIMED(c, FVM_K_MOMENTUM, 1, launch_momentum<R>(g, c->ph, c->tb, X, (R*)c->kappa, M[0], M[1], M[2],
                                               (R*)ustar[0], (R*)ustar[1], (R*)ustar[2], c->dt_dev, s));
   return cuda_check(c, "stage predictor");
@@ -1166,7 +1200,7 @@ fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* 
   // 2. curvature and smoothed alpha of the stage input
   double* M[3] = {(double*)c->M[0], (double*)c->M[1], (double*)c->M[2]};
   const int passes = c->prm.smooth_passes;
-  TIMED(c, FVM_K_INTERFACE, 1, launch_interface<double>(g, c->ph, c->tb, passes, X[3], X[4],
+  TIMED(c, FVM_K_INTERFACE, 1, launch_interface<double>(g, c->ph, c->tb, passes, X[3], X[4], nullptr,
                                                      (double*)c->kappa, M[0], M[1], M[2], s));
   const double* at = X[3];
   if (passes == 1) {
@@ -1247,7 +1281,7 @@ fvm_status step_adjoint_impl(fvm_ctx* c, const fvm_state* st_n, long step_index,
   cudaError_t ce =
       cudaMemcpyAsync(c->apf, st_n->p, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (ce != cudaSuccess) return set_err(c, FVM_ECUDA, cudaGetErrorString(ce));
-  void* sp[5] = {st_n->u, st_n->v, st_n->w, st_n->alpha, st_n->T};
+  void* sp[6] = {st_n->u, st_n->v, st_n->w, st_n->alpha, st_n->T, nullptr};
   Fields<double> Sn = fields_of<double>(sp);
   Fields<double> A = fields_of<double>(c->A);
   Fields<double> B = fields_of<double>(c->B);

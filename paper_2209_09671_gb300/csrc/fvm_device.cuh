@@ -132,6 +132,7 @@ struct PhysR {
   R eps_a, eps_T, eps_u, eps_n;
   R L[3];
   R h, ih;
+  R dsdc, c0, diff_c[2], eps_c;
 };
 
 template <typename R>
@@ -156,6 +157,11 @@ inline PhysR<R> make_physr(const Phys& ph, const Geo& g) {
   q.eps_n = (R)ph.eps_n;
   q.h = (R)g.h;
   q.ih = (R)g.ih;
+  q.dsdc = (R)ph.dsdc;
+  q.c0 = (R)ph.c0;
+  q.diff_c[0] = (R)ph.diff_c[0];
+  q.diff_c[1] = (R)ph.diff_c[1];
+  q.eps_c = (R)ph.eps_c;
   return q;
 }
 
@@ -168,6 +174,19 @@ __device__ __forceinline__ R mixr(R alpha, const R* pair) {
 template <typename R>
 __device__ __forceinline__ R sigma_r(R T, const PhysR<R>& q) {
   return q.sigma0 + q.dsdT * (T - q.T0);
+}
+
+// sigma(c, T) of Eq. 5 with the solutal term
+template <typename R>
+__device__ __forceinline__ R sigma_rc(R T, R c, const PhysR<R>& q) {
+  return q.sigma0 + q.dsdT * (T - q.T0) + q.dsdc * (c - q.c0);
+}
+
+// harmonic face mean 2 a b / (a + b), 0 where both vanish
+template <typename R>
+__device__ __forceinline__ R harmonic(R a, R b) {
+  const R s = a + b;
+  return s > R(0) ? R(2) * a * b / s : R(0);
 }
 
 // WENO5-JS value at the face right of v0 from cells v0-2 .. v0+2 (left bias),

@@ -46,14 +46,19 @@ struct Phys {
   double eps_a, eps_T, eps_u;             // WENO eps per field
   double eps_n;                           // normal regulariser 1e-8 / h
   double L[3];                            // domain lengths
+  double dsdc, c0;                        // sigma += dsdc (c - c0) with a concentration
+  double diff_c[2];                       // diffusivity of c per phase
+  double eps_c;                           // WENO eps of c
 };
 
-// Pointers of one state (u, v, w, alpha, T) in the working precision R.
+// Pointers of one state (u, v, w, alpha, T and the concentration c, null
+// when there is none) in the working precision R.
 template <typename R>
 struct Fields {
   R* u[3];
   R* alpha;
   R* T;
+  R* c;
 };
 
 // One multigrid level in precision T.
@@ -78,11 +83,22 @@ void launch_smooth(const Geo& g, const R* in, R* out, cudaStream_t s);
 // smoothing (passes 0..2), face normals, curvature and Marangoni vector
 template <typename R>
 void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, int passes, const R* alpha,
-                      const R* T, R* kappa, R* M0, R* M1, R* M2, cudaStream_t s);
+                      const R* T, const R* c, R* kappa, R* M0, R* M1, R* M2, cudaStream_t s);
+// fct_p / fct_m: limiter ratios of the bounded alpha transport (null: WENO5)
 template <typename R>
 void launch_scalars(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, Fields<R> Sn,
                     Fields<R> Y, const double* dt, double a, double b, double xc_shift,
-                    cudaStream_t s);
+                    const R* fct_p, const R* fct_m, cudaStream_t s);
+// limiter ratios R+, R- of the bounded alpha transport (flux-corrected
+// blend of upwind and WENO5 fluxes with the bounds 0 and 1)
+template <typename R>
+void launch_fct_ratios(const Geo& g, const Phys& ph, Fields<R> X, const double* dt, R* Rp, R* Rm,
+                       cudaStream_t s);
+// transport of the concentration c (WENO5 advection, diffusion) and its stage
+// update Y.c = a Sn.c + b (X.c + dt R_c)
+template <typename R>
+void launch_concentration(const Geo& g, const Phys& ph, Fields<R> X, Fields<R> Sn, Fields<R> Y,
+                          const double* dt, double a, double b, cudaStream_t s);
 template <typename R>
 void launch_momentum(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, const R* kappa,
                      const R* M0, const R* M1, const R* M2, R* us0, R* us1, R* us2,

@@ -205,6 +205,7 @@ struct IfaceShared {
   R s1[Tile<2>::N];         // after the first [1,2,1]/4 pass
   R s2[Tile<1>::N];         // smoothed alpha
   R T[Tile<1>::N];
+  R c[Tile<1>::N];          // concentration (when transported)
   R nx[kBZ][kBY][kBX + 1];  // face normals
   R ny[kBZ][kBY + 1][kBX];
   R nz[kBZ + 1][kBY][kBX];
@@ -281,12 +282,13 @@ __device__ __forceinline__ R face_normal(const R* __restrict__ s2, int lx, int l
 template <typename R>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     k_interface(Geo g, PhysR<R> ph, TBC tb, int passes, const R* __restrict__ alpha,
-                const R* __restrict__ T, R* __restrict__ kappa, R* __restrict__ M0,
-                R* __restrict__ M1, R* __restrict__ M2) {
+                const R* __restrict__ T, const R* __restrict__ conc, R* __restrict__ kappa,
+                R* __restrict__ M0, R* __restrict__ M1, R* __restrict__ M2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   IfaceShared<R>& S = *reinterpret_cast<IfaceShared<R>*>(smem_raw);
   stage<3, F_EVEN, 0>(S.a, alpha, g, tb);
   stage<1, F_TEMP, 0>(S.T, T, g, tb);
+  if (conc) stage<1, F_EVEN, 0>(S.c, conc, g, tb);
   __syncthreads();
   if (passes >= 1) {
     smooth_pass<3, 2>(g, S.a, S.s1);
@@ -337,8 +339,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     // linear sigma(T): the difference of two neighbouring temperatures is
     // exact, while sigma0 + dsigma/dT (T - T0) rounded to float at
     // sigma ~ 1.9 keeps only ~4 digits of a variation of ~1e-3
-    if (sizeof(R) == 4) sv[d] = ph.dsdT * (Tp - Tm) * i2h;
-    else sv[d] = (sigma_r(Tp, ph) - sigma_r(Tm, ph)) * i2h;
+    if (conc) {
+      // sigma(c, T) of Eq. 5: in float the exact neighbour differences
+      // again, in double the difference of the two cells' sigma values
+      const R cp = S.c[Tile<1>::at(tx + ox, ty + oy, tz + oz)];
+      const R cm = S.c[Tile<1>::at(tx - ox, ty - oy, tz - oz)];
+      if (sizeof(R) == 4) sv[d] = (ph.dsdT * (Tp - Tm) + ph.dsdc * (cp - cm)) * i2h;
+      else sv[d] = (sigma_rc(Tp, cp, ph) - sigma_rc(Tm, cm, ph)) * i2h;
+    } else if (sizeof(R) == 4) {
+      sv[d] = ph.dsdT * (Tp - Tm) * i2h;
+    } else {
+      sv[d] = (sigma_r(Tp, ph) - sigma_r(Tm, ph)) * i2h;
+    }
   }
   R gn = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
   R tn = sqrt(tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]) + epsn;
@@ -351,13 +363,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
 
 template <typename R>
 void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, int passes, const R* alpha,
-                      const R* T, R* kappa, R* M0, R* M1, R* M2, cudaStream_t s) {
+                      const R* T, const R* c, R* kappa, R* M0, R* M1, R* M2, cudaStream_t s) {
   const int smem = (int)sizeof(IfaceShared<R>);
   cudaFuncSetAttribute(k_interface<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   cudaFuncSetAttribute(k_interface<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   k_interface<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
-      g, make_physr<R>(ph, g), tb, passes, alpha, T, kappa, M0, M1, M2);
+      g, make_physr<R>(ph, g), tb, passes, alpha, T, c, kappa, M0, M1, M2);
 }
 
 // ---------------------------------------------------------------------------
@@ -380,9 +392,40 @@ struct ScalShared {
 
 // advective fluxes of alpha and T and the conductive flux of T through the
 // low D-face of local cell (lx,ly,lz)
+// limiter ratios of the bounded phase-fraction option (null: plain WENO5)
+template <typename R>
+struct FctRatios {
+  const R* Rp;   // R+ per cell: fraction of the incoming antidiffusive flux allowed
+  const R* Rm;   // R- per cell: fraction of the outgoing antidiffusive flux allowed
+};
+
+// flux-corrected alpha flux through the low D-face of global cell (i,j,k)
+// (Zalesak 1979 with the bounds 0 and 1): between the upwind flux F_L and
+// the WENO5 flux F_H, F = F_L + theta (F_H - F_L) with theta from the
+// limiter ratios of the face's two cells
+template <int D, typename R>
+__device__ __forceinline__ R fct_flux(const FctRatios<R>& f, const Geo& g, bool in, int i, int j,
+                                      int k, R U, R aL, R aR, R FH) {
+  const R FL = U >= R(0) ? U * aL : U * aR;
+  const R A = FH - FL;
+  int li = i, lj = j, lk = k;
+  shift<D>(li, lj, lk, -1);
+  R th = R(1);
+  if (A > R(0)) {
+    const R rpR = g_even(f.Rp, g, in, i, j, k), rmL = g_even(f.Rm, g, in, li, lj, lk);
+    th = rpR < rmL ? rpR : rmL;
+  } else if (A < R(0)) {
+    const R rpL = g_even(f.Rp, g, in, li, lj, lk), rmR = g_even(f.Rm, g, in, i, j, k);
+    th = rpL < rmR ? rpL : rmR;
+  }
+  return FL + th * A;
+}
+
 template <int D, typename R>
 __device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<R>& ph, const R Uf,
-                                            int lx, int ly, int lz, R& Fa, R& FT, R& Df) {
+                                            int lx, int ly, int lz, R& Fa, R& FT, R& Df,
+                                            const FctRatios<R>& fct, const Geo& g, bool in,
+                                            int gi, int gj, int gk) {
   const int dx = D == 0, dy = D == 1, dz = D == 2;
   R av[6], tv[6];
 #pragma unroll
@@ -392,6 +435,7 @@ __device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<
     tv[m] = S.T[Tile<3>::at(lx + o * dx, ly + o * dy, lz + o * dz)];
   }
   Fa = upwind_flux(Uf, av, ph.eps_a);
+  if (fct.Rp) Fa = fct_flux<D>(fct, g, in, gi, gj, gk, Uf, av[2], av[3], Fa);
   FT = upwind_flux(Uf, tv, ph.eps_T);
   R lL = mixr(av[2], ph.lam), lR = mixr(av[3], ph.lam);
   R lf = R(2) * lL * lR / (lL + lR);
@@ -401,7 +445,8 @@ __device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<
 template <typename R>
 __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
     k_scalars(Geo g, PhysR<R> ph, TBC tb, Fields<R> X, Fields<R> Sn, Fields<R> Y,
-              const double* __restrict__ dtp, R a, R b, R xc, R yc, R qamp, R ir2) {
+              const double* __restrict__ dtp, R a, R b, R xc, R yc, R qamp, R ir2,
+              FctRatios<R> fct) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScalShared<R>& S = *reinterpret_cast<ScalShared<R>*>(smem_raw);
   stage<3, F_EVEN, 0>(S.a, X.alpha, g, tb);
@@ -415,22 +460,25 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
   const R ih = ph.ih;
   ScalFlux<R>& F = S.F;
   if (i <= nx && j < ny && k < nz) {
-    scalar_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i, j, k), tx, ty, tz, F.x[0][tz][ty][tx], F.x[1][tz][ty][tx], F.x[2][tz][ty][tx]);
+    scalar_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i, j, k), tx, ty, tz, F.x[0][tz][ty][tx], F.x[1][tz][ty][tx], F.x[2][tz][ty][tx],
+                   fct, g, in, i, j, k);
     if (tx == kBX - 1 && i + 1 <= nx)
       scalar_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i + 1, j, k), tx + 1, ty, tz, F.x[0][tz][ty][tx + 1], F.x[1][tz][ty][tx + 1],
-                     F.x[2][tz][ty][tx + 1]);
+                     F.x[2][tz][ty][tx + 1], fct, g, in, i + 1, j, k);
   }
   if (i < nx && j <= ny && k < nz) {
-    scalar_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j, k), tx, ty, tz, F.y[0][tz][ty][tx], F.y[1][tz][ty][tx], F.y[2][tz][ty][tx]);
+    scalar_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j, k), tx, ty, tz, F.y[0][tz][ty][tx], F.y[1][tz][ty][tx], F.y[2][tz][ty][tx],
+                   fct, g, in, i, j, k);
     if (ty == kBY - 1 && j + 1 <= ny)
       scalar_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j + 1, k), tx, ty + 1, tz, F.y[0][tz][ty + 1][tx], F.y[1][tz][ty + 1][tx],
-                     F.y[2][tz][ty + 1][tx]);
+                     F.y[2][tz][ty + 1][tx], fct, g, in, i, j + 1, k);
   }
   if (i < nx && j < ny && k <= nz) {
-    scalar_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k), tx, ty, tz, F.z[0][tz][ty][tx], F.z[1][tz][ty][tx], F.z[2][tz][ty][tx]);
+    scalar_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k), tx, ty, tz, F.z[0][tz][ty][tx], F.z[1][tz][ty][tx], F.z[2][tz][ty][tx],
+                   fct, g, in, i, j, k);
     if (tz == kBZ - 1 && k + 1 <= nz)
       scalar_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k + 1), tx, ty, tz + 1, F.z[0][tz + 1][ty][tx], F.z[1][tz + 1][ty][tx],
-                     F.z[2][tz + 1][ty][tx]);
+                     F.z[2][tz + 1][ty][tx], fct, g, in, i, j, k + 1);
   }
   __syncthreads();
   if (i >= nx || j >= ny || k >= nz) return;
@@ -468,7 +516,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
 
 template <typename R>
 void launch_scalars(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, Fields<R> Sn,
-                    Fields<R> Y, const double* dt, double a, double b, double xc, cudaStream_t s) {
+                    Fields<R> Y, const double* dt, double a, double b, double xc, const R* fct_p,
+                    const R* fct_m, cudaStream_t s) {
   // source amplitude 2P/(pi r^2) and 1/r^2 formed once on the host
   double r2 = ph.q_radius * ph.q_radius;
   double qamp = ph.q_power != 0.0 ? 2.0 * ph.q_power / (M_PI * r2) : 0.0;
@@ -478,7 +527,161 @@ void launch_scalars(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, Fi
   cudaFuncSetAttribute(k_scalars<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   k_scalars<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
-      g, make_physr<R>(ph, g), tb, X, Sn, Y, dt, (R)a, (R)b, (R)xc, (R)ph.q_y0, (R)qamp, (R)ir2);
+      g, make_physr<R>(ph, g), tb, X, Sn, Y, dt, (R)a, (R)b, (R)xc, (R)ph.q_y0, (R)qamp, (R)ir2,
+      FctRatios<R>{fct_p, fct_m});
+}
+
+// limiter ratios of the bounded alpha transport for one stage: per cell the
+// upwind (low-order) update alpha_td and the antidiffusive fluxes of its six
+// faces give R+ = clamp((1 - alpha_td) h / dt / P+, 0, 1) and
+// R- = clamp(alpha_td h / dt / P-, 0, 1) (0 where P vanishes), P+- the sums
+// of antidiffusive fluxes into and out of the cell
+template <int D, typename R>
+__device__ __forceinline__ void fct_cell_face(const Geo& g, const PhysR<R>& ph, const R* alpha,
+                                              const R* u, int i, int j, int k, int s, R& FLo,
+                                              R& Ao) {
+  int fi = i, fj = j, fk = k;
+  shift<D>(fi, fj, fk, s);                   // the low face of cell c + s e_D
+  const R U = ld_vel<D>(u, g, fi, fj, fk);
+  R v[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    int a = fi, b = fj, cc = fk;
+    shift<D>(a, b, cc, m - 3);
+    v[m] = ld_even(alpha, g, a, b, cc);
+  }
+  const R FH = upwind_flux(U, v, ph.eps_a);
+  FLo = U >= R(0) ? U * v[2] : U * v[3];
+  Ao = FH - FLo;
+}
+
+template <typename R>
+__global__ void k_fct_ratios(Geo g, PhysR<R> ph, Fields<R> X, const double* __restrict__ dtp,
+                             R* __restrict__ Rp, R* __restrict__ Rm) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y,
+            k = blockIdx.z * kBZ + threadIdx.z;
+  if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) return;
+  const R dt = (R)dtp[0];
+  R div = 0, Pp = 0, Pm = 0;
+  R FL0, A0, FL1, A1;
+  fct_cell_face<0>(g, ph, X.alpha, X.u[0], i, j, k, 0, FL0, A0);
+  fct_cell_face<0>(g, ph, X.alpha, X.u[0], i, j, k, 1, FL1, A1);
+  div += (FL1 - FL0) * ph.ih;
+  Pp += (A0 > R(0) ? A0 : R(0)) + (-A1 > R(0) ? -A1 : R(0));
+  Pm += (-A0 > R(0) ? -A0 : R(0)) + (A1 > R(0) ? A1 : R(0));
+  fct_cell_face<1>(g, ph, X.alpha, X.u[1], i, j, k, 0, FL0, A0);
+  fct_cell_face<1>(g, ph, X.alpha, X.u[1], i, j, k, 1, FL1, A1);
+  div += (FL1 - FL0) * ph.ih;
+  Pp += (A0 > R(0) ? A0 : R(0)) + (-A1 > R(0) ? -A1 : R(0));
+  Pm += (-A0 > R(0) ? -A0 : R(0)) + (A1 > R(0) ? A1 : R(0));
+  fct_cell_face<2>(g, ph, X.alpha, X.u[2], i, j, k, 0, FL0, A0);
+  fct_cell_face<2>(g, ph, X.alpha, X.u[2], i, j, k, 1, FL1, A1);
+  div += (FL1 - FL0) * ph.ih;
+  Pp += (A0 > R(0) ? A0 : R(0)) + (-A1 > R(0) ? -A1 : R(0));
+  Pm += (-A0 > R(0) ? -A0 : R(0)) + (A1 > R(0) ? A1 : R(0));
+  const long long c = lin(g, i, j, k);
+  const R atd = X.alpha[c] - dt * div;
+  const R Qp = (R(1) - atd) * ph.h / dt, Qm = atd * ph.h / dt;
+  R rp = R(0), rm = R(0);
+  if (Pp > R(0)) rp = fmin(R(1), fmax(R(0), Qp / Pp));
+  if (Pm > R(0)) rm = fmin(R(1), fmax(R(0), Qm / Pm));
+  Rp[c] = rp;
+  Rm[c] = rm;
+}
+
+template <typename R>
+void launch_fct_ratios(const Geo& g, const Phys& ph, Fields<R> X, const double* dt, R* Rp, R* Rm,
+                       cudaStream_t s) {
+  k_fct_ratios<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), 0, s>>>(g, make_physr<R>(ph, g), X, dt, Rp,
+                                                                 Rm);
+}
+
+// ---------------------------------------------------------------------------
+// transport of a concentration c (the solutal field of Eq. 5): WENO5
+// advection with the face velocity, diffusion with the harmonic face mean of
+// the mixture diffusivity, no flux through walls (even ghosts), stage update
+template <typename R>
+struct ConcShared {
+  R c[Tile<3>::N];
+  R D[Tile<1>::N];                       // mixture diffusivity of the cells
+  R fx[2][kBZ][kBY][kBX + 1];            // [0] advective, [1] diffusive face fluxes
+  R fy[2][kBZ][kBY + 1][kBX];
+  R fz[2][kBZ + 1][kBY][kBX];
+};
+
+template <int D, typename R>
+__device__ __forceinline__ void conc_face(const ConcShared<R>& S, const PhysR<R>& ph, const R Uf,
+                                          int lx, int ly, int lz, R& Fa, R& Fd) {
+  const int dx = D == 0, dy = D == 1, dz = D == 2;
+  R v[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const int o = m - 3;
+    v[m] = S.c[Tile<3>::at(lx + o * dx, ly + o * dy, lz + o * dz)];
+  }
+  Fa = upwind_flux(Uf, v, ph.eps_c);
+  const R dL = S.D[Tile<1>::at(lx - dx, ly - dy, lz - dz)], dR = S.D[Tile<1>::at(lx, ly, lz)];
+  Fd = harmonic(dL, dR) * (v[3] - v[2]) * ph.ih;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    k_concentration(Geo g, PhysR<R> ph, Fields<R> X, Fields<R> Sn, Fields<R> Y,
+                    const double* __restrict__ dtp, R a, R b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ConcShared<R>& S = *reinterpret_cast<ConcShared<R>*>(smem_raw);
+  TBC tb;
+  tb.axis = -1;
+  stage<3, F_EVEN, 0>(S.c, X.c, g, tb);
+  stage<1, F_EVEN, 0>(S.D, X.alpha, g, tb);
+  __syncthreads();
+  for (int e = flat_tid(); e < Tile<1>::N; e += kThreads) S.D[e] = mixr(S.D[e], ph.diff_c);
+  const bool in = tile_interior(g, 3);
+  __syncthreads();
+  const R dt = (R)dtp[0];
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  if (i <= nx && j < ny && k < nz) {
+    conc_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i, j, k), tx, ty, tz, S.fx[0][tz][ty][tx], S.fx[1][tz][ty][tx]);
+    if (tx == kBX - 1 && i + 1 <= nx)
+      conc_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i + 1, j, k), tx + 1, ty, tz, S.fx[0][tz][ty][tx + 1],
+                   S.fx[1][tz][ty][tx + 1]);
+  }
+  if (i < nx && j <= ny && k < nz) {
+    conc_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j, k), tx, ty, tz, S.fy[0][tz][ty][tx], S.fy[1][tz][ty][tx]);
+    if (ty == kBY - 1 && j + 1 <= ny)
+      conc_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j + 1, k), tx, ty + 1, tz, S.fy[0][tz][ty + 1][tx],
+                   S.fy[1][tz][ty + 1][tx]);
+  }
+  if (i < nx && j < ny && k <= nz) {
+    conc_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k), tx, ty, tz, S.fz[0][tz][ty][tx], S.fz[1][tz][ty][tx]);
+    if (tz == kBZ - 1 && k + 1 <= nz)
+      conc_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k + 1), tx, ty, tz + 1, S.fz[0][tz + 1][ty][tx],
+                   S.fz[1][tz + 1][ty][tx]);
+  }
+  __syncthreads();
+  if (i >= nx || j >= ny || k >= nz) return;
+  const int c = (k * ny + j) * nx + i;
+  const R ih = ph.ih;
+  R Ra = 0, Dif = 0;
+  Ra -= (S.fx[0][tz][ty][tx + 1] - S.fx[0][tz][ty][tx]) * ih;
+  Dif += (S.fx[1][tz][ty][tx + 1] - S.fx[1][tz][ty][tx]) * ih;
+  Ra -= (S.fy[0][tz][ty + 1][tx] - S.fy[0][tz][ty][tx]) * ih;
+  Dif += (S.fy[1][tz][ty + 1][tx] - S.fy[1][tz][ty][tx]) * ih;
+  Ra -= (S.fz[0][tz + 1][ty][tx] - S.fz[0][tz][ty][tx]) * ih;
+  Dif += (S.fz[1][tz + 1][ty][tx] - S.fz[1][tz][ty][tx]) * ih;
+  const R Ec = S.c[Tile<3>::at(tx, ty, tz)] + dt * (Ra + Dif);
+  Y.c[c] = a * Sn.c[c] + b * Ec;
+}
+
+template <typename R>
+void launch_concentration(const Geo& g, const Phys& ph, Fields<R> X, Fields<R> Sn, Fields<R> Y,
+                          const double* dt, double a, double b, cudaStream_t s) {
+  const int smem = (int)sizeof(ConcShared<R>);
+  cudaFuncSetAttribute(k_concentration<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_concentration<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
+      g, make_physr<R>(ph, g), X, Sn, Y, dt, (R)a, (R)b);
 }
 
 // ---------------------------------------------------------------------------
@@ -632,7 +835,10 @@ __device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>&
       sh1<D>(a, b, cc, -1);
       const R alL = g_even(X.alpha, g, in, a, b, cc), alR = X.alpha[c];
       const R rho_f = R(0.5) * (mixr(alL, ph.rho) + mixr(alR, ph.rho));
-      const R sig_f = R(0.5) * (sigma_r(g_T(X.T, g, tb, in, a, b, cc), ph) + sigma_r(X.T[c], ph));
+      const R TL = g_T(X.T, g, tb, in, a, b, cc), TR = X.T[c];
+      const R sig_f = X.c ? R(0.5) * (sigma_rc(TL, g_even(X.c, g, in, a, b, cc), ph) +
+                                      sigma_rc(TR, X.c[c], ph))
+                          : R(0.5) * (sigma_r(TL, ph) + sigma_r(TR, ph));
       const R kap_f = R(0.5) * (g_even(kappa, g, in, a, b, cc) + kappa[c]);
       const R jump = (alR - alL) * ih;
       const R fn = -sig_f * kap_f * jump;
@@ -817,9 +1023,15 @@ __global__ void k_dt_reduce(Geo g, Phys ph, Fields<R> X, unsigned long long* __r
     v[2] = fabs((double)X.u[2][c]);
     R al = X.alpha[c];
     R T = X.T[c];
-    v[3] = fabs((double)sigma_of_T(T, ph));
+    R sg = sigma_of_T(T, ph);
+    if (X.c) sg += (R)ph.dsdc * (X.c[c] - (R)ph.c0);
+    v[3] = fabs((double)sg);
     v[4] = (double)(mixp(al, ph.mu) / mixp(al, ph.rho));
     v[5] = (double)(mixp(al, ph.lam) / mixp(al, ph.rcp));
+    if (X.c) {   // the concentration's diffusion shares the diffusive limit
+      const double dc = (double)mixp(al, ph.diff_c);
+      v[5] = dc > v[5] ? dc : v[5];
+    }
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       if (!(v[q] <= 1.7976931348623157e308)) bad = 1;
@@ -907,7 +1119,7 @@ __global__ void k_diagnostics(Geo g, Phys ph, Fields<R> X, const double* __restr
     unsigned long long bits = (unsigned long long)__double_as_longlong(adv);
     mdiv = bits > mdiv ? bits : mdiv;
     double chk = (double)X.u[0][c] + (double)X.u[1][c] + (double)X.u[2][c] + (double)al +
-                 (double)X.T[c] + p[c];
+                 (double)X.T[c] + p[c] + (X.c ? (double)X.c[c] : 0.0);
     if (!(fabs(chk) <= 1.7976931348623157e308) || !(adv <= 1.7976931348623157e308)) bad = 1;
   }
   double s1 = block_sum(sa);
@@ -936,10 +1148,14 @@ void launch_diagnostics(const Geo& g, const Phys& ph, Fields<R> X, const double*
 #define FVM_INST(R)                                                                              \
   template void launch_smooth<R>(const Geo&, const R*, R*, cudaStream_t);                        \
   template void launch_interface<R>(const Geo&, const Phys&, const TBC&, int, const R*,          \
-                                    const R*, R*, R*, R*, R*, cudaStream_t);                     \
+                                    const R*, const R*, R*, R*, R*, R*, cudaStream_t);           \
+  template void launch_concentration<R>(const Geo&, const Phys&, Fields<R>, Fields<R>,           \
+                                        Fields<R>, const double*, double, double, cudaStream_t); \
   template void launch_scalars<R>(const Geo&, const Phys&, const TBC&, Fields<R>, Fields<R>,     \
-                                  Fields<R>, const double*, double, double, double,              \
-                                  cudaStream_t);                                                 \
+                                  Fields<R>, const double*, double, double, double, const R*,    \
+                                  const R*, cudaStream_t);                                       \
+  template void launch_fct_ratios<R>(const Geo&, const Phys&, Fields<R>, const double*, R*, R*,  \
+                                     cudaStream_t);                                              \
   template void launch_momentum<R>(const Geo&, const Phys&, const TBC&, Fields<R>, const R*,     \
                                    const R*, const R*, const R*, R*, R*, R*, const double*,      \
                                    cudaStream_t);                                                \

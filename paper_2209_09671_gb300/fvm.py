@@ -43,12 +43,18 @@ class fvm_params(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("mx_inner_cycles", ctypes.c_int),
         ("adjoint", ctypes.c_int),
+        ("concentration", ctypes.c_int),
+        ("dsigma_dc", ctypes.c_double), ("c0", ctypes.c_double),
+        ("diff_c", ctypes.c_double * 2),
+        ("weno_scale_c", ctypes.c_double),
+        ("alpha_scheme", ctypes.c_int),
     ]
 
 
 class fvm_state(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p),
-                ("alpha", ctypes.c_void_p), ("T", ctypes.c_void_p), ("p", ctypes.c_void_p)]
+                ("alpha", ctypes.c_void_p), ("T", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("c", ctypes.c_void_p)]
 
 
 class fvm_step_info(ctypes.Structure):
@@ -155,6 +161,12 @@ def make_params(p) -> fvm_params:
     c.precision = int(p.precision)
     c.mx_inner_cycles = int(p.mx_inner_cycles)
     c.adjoint = int(getattr(p, "adjoint", 0))
+    c.concentration = int(getattr(p, "concentration", 0))
+    c.dsigma_dc = float(getattr(p, "dsigma_dc", 0.0))
+    c.c0 = float(getattr(p, "c0", 0.0))
+    c.diff_c[:] = [float(v) for v in getattr(p, "diff_c", (0.0, 0.0))]
+    c.weno_scale_c = float(getattr(p, "weno_scale_c", 1.0))
+    c.alpha_scheme = int(getattr(p, "alpha_scheme", 0))
     return c
 
 
@@ -182,6 +194,7 @@ class Solver:
         self.params = params
         self.cparams = make_params(params)
         self.mixed = int(params.precision) == MIXED
+        self.conc = int(getattr(params, "concentration", 0)) == 1
         self.rdtype = torch.float32 if self.mixed else torch.float64
         nbytes = fvm_workspace_size(self.cparams)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
@@ -202,7 +215,7 @@ class Solver:
     def _state(self, s, need_p=True) -> fvm_state:
         import torch
         st = fvm_state()
-        for k in FIELDS5:
+        for k in FIELDS5 + (("c",) if self.conc and "c" in s else ()):
             t = s[k]
             if not (t.is_cuda and t.dtype == self.rdtype and t.is_contiguous()):
                 raise ValueError(f"field {k} must be a contiguous CUDA {self.rdtype} tensor")
