@@ -7,10 +7,15 @@ operators.
 The projection solve enters through ``_Solve``: its forward is the oracle's
 multigrid solve converged to ``rtol`` (not a fixed number of cycles), and its
 backward applies the same solve to the incoming gradient -- the operator
-L = -D beta G is symmetric, and the mean removal before and after the solve is
-an orthogonal projector, so the adjoint of b -> p is the solve itself.  This
-holds for equal phase densities (beta constant), the setting this adjoint
-supports; the dt is fixed.
+L = -D beta G is symmetric for any face coefficients beta, and the mean
+removal before and after the solve is an orthogonal projector, so the
+adjoint of b -> p is the solve itself.  With unequal phase densities beta
+depends on alpha: p = L^+ b gives dp = -L^+ (dL) p, so the gradient of a
+face coefficient is -(gb_R - gb_L)(p_R - p_L)/h^2 with gb = L^+ (dJ/dp)
+(the bilinear form of L), and autograd carries it on to alpha through
+beta = 1/rho_f; every other property of the mixture (mu, lambda, rho c_p)
+is differentiated by autograd through the oracle's own operators.  The dt is
+fixed.
 """
 from __future__ import annotations
 
@@ -21,26 +26,35 @@ from . import fvm_oracle as O
 
 class _Solve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, b, alpha, prm, grid, rtol):
+    def forward(ctx, b, alpha, prm, grid, rtol, beta0, beta1, beta2):
         q = prm.replace(mg_rtol=rtol, mg_fixed_cycles=0, mg_max_cycles=400)
         b = b - b.mean()
         p, _, _ = O.mg_solve(alpha.detach(), b.detach(), torch.zeros_like(b), q, grid)
-        ctx.saved = (alpha.detach(), q, grid)
+        ctx.saved = (alpha.detach(), q, grid, p)
         return p
 
     @staticmethod
     def backward(ctx, gp):
-        alpha, q, grid = ctx.saved
+        alpha, q, grid, p = ctx.saved
         g = gp - gp.mean()
         gb, _, _ = O.mg_solve(alpha, g, torch.zeros_like(g), q, grid)
-        return gb - gb.mean(), None, None, None, None
+        gb = gb - gb.mean()
+        gbeta = []
+        for d in range(3):
+            if grid.n[d] == 1:
+                gbeta.append(torch.zeros_like(p))
+                continue
+            w = 1.0 / (grid.h * grid.h)
+            # low d-face of cell c: L = c - e_d, R = c
+            gbeta.append(-(gb - O._roll_dn(gb, d)) * (p - O._roll_dn(p, d)) * w)
+        return (gb, None, None, None, None) + tuple(gbeta)
 
 
 def _projection(vel_star, alpha, prm, grid, dt, rtol):
     h = grid.h
     b = -O.divergence(vel_star, grid) / dt
-    p = _Solve.apply(b, alpha, prm, grid, rtol)
-    beta = O.fine_beta(alpha.detach(), prm, grid)
+    beta = O.fine_beta(alpha, prm, grid)
+    p = _Solve.apply(b, alpha, prm, grid, rtol, *beta)
     out = []
     for d in range(3):
         u = vel_star[d] - dt * beta[d] * (p - O._roll_dn(p, d)) / h
@@ -73,8 +87,6 @@ FIELDS = ("u", "v", "w", "alpha", "T")
 def step_vjp(state, prm, step_index, dt, lam, rtol=1e-13):
     """(lambda_n, dtheta) with lambda_n = (dS_{n+1}/dS_n)^T lam and
     dtheta = (dS_{n+1}/dtheta)^T lam, theta = (dsigma/dT, q_power)."""
-    if prm.rho[0] != prm.rho[1]:
-        raise ValueError("the oracle adjoint supports equal phase densities")
     S = {k: O._t(state[k]).clone().requires_grad_(True) for k in FIELDS}
     th = [torch.tensor(float(prm.dsigma_dT), dtype=O.DT, requires_grad=True),
           torch.tensor(float(prm.q_power), dtype=O.DT, requires_grad=True)]

@@ -20,8 +20,20 @@ def _forward(state, prm, dt):
         return A.differentiable_step(S, prm, 2, dt, rtol=1e-13)
 
 
-def test_step_vjp_matches_central_differences():
+import pytest
+
+CASES = {
+    "equal": {},
+    # unequal phase densities (the d L / d alpha term of the projection) and
+    # unequal viscosity, conductivity and heat capacity
+    "density_ratio_10": dict(rho=(1.0, 10.0), mu=(0.5, 1.5), lam=(0.7, 1.3), cp=(2.0, 0.3)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_step_vjp_matches_central_differences(case):
     p, s = cases.adjoint_channel(nx=8, ny=8, nz=8)
+    p = p.replace(**CASES[case])
     s["u"][:] = 0.02 * cases.uniform(5, p.shape, -1, 1)
     s["v"][:] = 0.02 * cases.uniform(6, p.shape, -1, 1)
     s["w"][:] = 0.02 * cases.uniform(7, p.shape, -1, 1)
@@ -42,7 +54,9 @@ def test_step_vjp_matches_central_differences():
     # parameters
     for i, name in enumerate(("dsigma_dT", "q_power")):
         v = getattr(p, name)
-        eps = 1e-4 * abs(v)
+        # a step of 1e-3 |theta|: O(eps^2) truncation ~1e-7 relative, well above
+        # the rounding of J left by the 1e-13 solves
+        eps = 1e-3 * abs(v)
         fp = _inner(lam, _forward(s, p.replace(**{name: v + eps}), dt))
         fm = _inner(lam, _forward(s, p.replace(**{name: v - eps}), dt))
         fd = (fp - fm) / (2 * eps)
