@@ -220,13 +220,18 @@ fvm_status fvm_stage_predict(fvm_ctx* ctx, const fvm_state* X, long step_index, 
  * (written, must not alias lam_np1): device double fields, layout as the
  * state; their p members are ignored.  dtheta: host, 2 doubles, ACCUMULATED
  * into (the caller zeroes them).  The stages are recomputed from st_n; the
- * three projections are adjoined by the same multigrid solve (the operator
- * is symmetric for constant beta).  Requirements, else an error and no
+ * three projections are adjoined by the same multigrid solve: with
+ * u = P u*, P = I + beta G L^+ D, the adjoint of u* is P^T = I + G L^+ D beta
+ * (L = -D beta G is symmetric); with unequal densities beta = 1/rho_f
+ * depends on alpha, and the derivative of both 1/rho_f factors (momentum
+ * predictor and projection) adds to the adjoint of alpha, using each
+ * stage's recomputed forward pressure.  Requirements, else an error and no
  * write: a context created with adjoint = 1 (EINVAL; fvm_create accepts
- * adjoint = 1 only with precision F64, and the workspace then holds 40 more
- * double fields of N cells), equal rho, mu, cp and lambda in both phases
- * (EUNSUPPORTED: the projection coefficient and the transport coefficients
- * are then constant), dt > 0 (EINVAL).  A projection that stops at
+ * adjoint = 1 only with precision F64, no concentration and alpha_scheme 0,
+ * and the workspace then holds 43 more double fields of N cells), equal mu,
+ * lambda and rho*cp in both phases (EUNSUPPORTED: the transport
+ * coefficients are then constant; the densities may differ), dt > 0
+ * (EINVAL).  A projection that stops at
  * mg_max_cycles above mg_rtol returns FVM_ENOCONV after completing the
  * sweep.  The derivative of |g| at g = 0 is taken as 0.  Entries of lam_n on
  * wall faces are 0.  Synchronises the context's stream. */

@@ -1,6 +1,8 @@
-// Reverse mode (adjoint) of one forward-Euler stage of the FP64 step, for the
-// equal-property setting (one rho, mu, lambda, c_p for both phases, so that
-// the projection coefficient is constant and the projection is self-adjoint).
+// Reverse mode (adjoint) of one forward-Euler stage of the FP64 step, for
+// phases of equal viscosity, conductivity and volumetric heat capacity rho
+// c_p (the transport coefficients are then constant); the densities may
+// differ, which makes the face coefficient beta = 1/rho_f of the momentum
+// predictor and of the projection depend on alpha (k_adj_density).
 //
 // Form of the work.  Every stencil flux is differentiated once, by the thread
 // that owns its location (a cell centre, a face or an edge), in two passes:
@@ -237,7 +239,7 @@ struct TangA {
 
 // adjoint of the advection (lA = dt lambda) and of the stress (lF = dt
 // lambda / rho_f) at the D-face (i, j, k); ghost faces and wall faces carry
-// none.  The adjoint requires equal phase densities, so rho_f = rho.
+// none.
 template <int D>
 __device__ __forceinline__ void face_weights(const AdjArgs& A, int i, int j, int k, double& lA,
                                              double& lF) {
@@ -253,8 +255,9 @@ __device__ __forceinline__ void face_weights(const AdjArgs& A, int i, int j, int
     }
   }
   if (g.bc[D] == WALL && c[D] == 0) return;
-  lA = A.dt * A.lus[D][lin3(g, c[0], c[1], c[2])];
-  lF = lA * A.irho;
+  const int f = lin3(g, c[0], c[1], c[2]);
+  lA = A.dt * A.lus[D][f];
+  lF = lA * A.beta[D][f];
 }
 
 // centre flux of component D at cell (i, j, k): slots q0 + m <- u_D at
@@ -417,8 +420,7 @@ __global__ void k_adj_mom_gather(AdjArgs A) {
 
 // CSF and Marangoni face forces: f = -sigma_f kappa_f (alpha_R - alpha_L)/h
 // + (M_D(L) + M_D(R))/2 on every D-face, each cell gathering the two faces
-// it touches (its own low face as R, the next face as L); rho_f = rho
-// (equal phase densities)
+// it touches (its own low face as R, the next face as L), scaled by 1/rho_f
 __global__ void k_adj_forces(AdjArgs A) {
   const Geo& g = A.g;
   const long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -442,7 +444,7 @@ __global__ void k_adj_forces(AdjArgs A) {
           const Ref rL = r_even(g, i - ox, j - oy, k - oz);
           const Ref tL = r_T(g, A.tb, i - ox, j - oy, k - oz);
           const double alL = val(A.X[3], rL), TL = val(A.X[4], tL), kL = val(A.kappa, rL);
-          const double lF = dt * lam * A.irho;
+          const double lF = dt * lam * A.beta[D][c];
           const double sL = A.sigma0 + A.dsdT * (TL - A.T0);
           const double jump = (alC - alL) * ih;
           const double sf = 0.5 * (sL + sC), kf = 0.5 * (kL + kC);
@@ -462,7 +464,7 @@ __global__ void k_adj_forces(AdjArgs A) {
         if (lam != 0.0) {
           const int R = rf.idx;
           const double alR = A.X[3][R], TR = A.X[4][R], kR = A.kappa[R];
-          const double lF = dt * lam * A.irho;
+          const double lF = dt * lam * A.beta[D][R];
           const double sR = A.sigma0 + A.dsdT * (TR - A.T0);
           const double jump = (alR - alC) * ih;
           const double sf = 0.5 * (sC + sR), kf = 0.5 * (kC + kR);
@@ -845,6 +847,96 @@ __global__ void k_adj_marangoni_gather(AdjArgs A) {
   A.lu[4][c] += aT;
 }
 
+// d/d alpha of the two 1/rho_f = beta_f factors of the stage.  With
+// mu = lus the adjoint of u*, the momentum predictor's dt (V + f) beta_f and
+// the projection's -dt beta_f (G p)_f give, per face, dt mu_f (Phi_f - (G p)_f)
+// d beta_f, where Phi_f = V + f_n + f_M and p is the stage's forward
+// pressure (the projection's adjoint is u* -> P^T; its derivative in beta is
+// -dt P (d beta G p)); d beta_f / d alpha_L,R = -beta_f^2 / 2 (rho_1 - rho_0)
+// on [0, 1] (the clamp of the mixture passes its bounds).  Each cell gathers
+// its low face (as R) and the next face (as L) in every direction.
+__global__ void k_adj_density(AdjArgs A, double drho) {
+  const Geo& g = A.g;
+  const long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (cl >= g.N) return;
+  const int c = (int)cl;
+  const double al = A.X[3][c];
+  if (!(al >= 0.0 && al <= 1.0)) return;
+  int i, j, k;
+  decode3(g, c, i, j, k);
+  const int gi[3] = {i, j, k};
+  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  double acc = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int n = g.n[d];
+    if (n == 1) continue;
+    // own low face f = c (skipped on a wall), then the next face (the low face
+    // of the neighbour above, wrapped; none above the last cell of a wall axis)
+    for (int side = 0; side < 2; ++side) {
+      int f;
+      if (side == 0) {
+        if (g.bc[d] == WALL && gi[d] == 0) continue;
+        f = c;
+      } else {
+        if (gi[d] == n - 1) {
+          if (g.bc[d] == WALL) continue;
+          f = c - (n - 1) * st[d];
+        } else {
+          f = c + st[d];
+        }
+      }
+      int fi, fj, fk;
+      decode3(g, f, fi, fj, fk);
+      const int fidx[3] = {fi, fj, fk};
+      const int lo = fidx[d] == 0 ? f + (n - 1) * st[d] : f - st[d];
+      const double gp = (A.pfw[f] - A.pfw[lo]) * g.ih;
+      const double b = A.beta[d][f];
+      acc += A.lus[d][f] * b * b * (A.phi[d][f] - gp);
+    }
+  }
+  A.lu[3][c] += -0.5 * drho * A.dt * acc;
+}
+
+
+__global__ void k_sub_grad(Geo g, const double* __restrict__ u0, const double* __restrict__ u1,
+                           const double* __restrict__ u2, const double* __restrict__ p,
+                           const double* __restrict__ dtp, double* __restrict__ o0,
+                           double* __restrict__ o1, double* __restrict__ o2) {
+  const long long cl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (cl >= g.N) return;
+  const int c = (int)cl;
+  int i, j, k;
+  decode3(g, c, i, j, k);
+  const int gi[3] = {i, j, k};
+  const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
+  const double* u[3] = {u0, u1, u2};
+  double* o[3] = {o0, o1, o2};
+  const double dth = dtp[0] * g.ih;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (g.bc[d] == WALL && gi[d] == 0) {
+      o[d][c] = 0.0;
+      continue;
+    }
+    const int lo = gi[d] == 0 ? c + (g.n[d] - 1) * st[d] : c - st[d];
+    o[d][c] = u[d][c] - (p[c] - p[lo]) * dth;
+  }
+}
+
+
+__global__ void k_face_mul(long long n, const double* __restrict__ b0, const double* __restrict__ b1,
+                           const double* __restrict__ b2, const double* __restrict__ u0,
+                           const double* __restrict__ u1, const double* __restrict__ u2,
+                           double* __restrict__ o0, double* __restrict__ o1, double* __restrict__ o2) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  o0[c] = b0[c] * u0[c];
+  o1[c] = b1[c] * u1[c];
+  o2[c] = b2[c] * u2[c];
+}
+
+
 __global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b,
                         double* __restrict__ y) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -864,6 +956,23 @@ __global__ void k_zero_wall_faces(Geo g, double* u0, double* u1, double* u2) {
 }
 
 }  // namespace
+
+int launch_adj_density(const AdjArgs& A, cudaStream_t s) {
+  k_adj_density<<<(unsigned)((A.g.N + 127) / 128), 128, 0, s>>>(A, A.rho[1] - A.rho[0]);
+  return 1;
+}
+
+void launch_sub_grad(const Geo& g, double* const* u, const double* p, const double* dt,
+                     double* const* out, cudaStream_t s) {
+  k_sub_grad<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(g, u[0], u[1], u[2], p, dt, out[0],
+                                                           out[1], out[2]);
+}
+
+void launch_face_mul(const Geo& g, double* const* beta, double* const* u, double* const* out,
+                     cudaStream_t s) {
+  k_face_mul<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(g.N, beta[0], beta[1], beta[2], u[0],
+                                                           u[1], u[2], out[0], out[1], out[2]);
+}
 
 static inline unsigned g1(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 

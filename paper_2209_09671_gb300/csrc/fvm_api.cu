@@ -173,6 +173,7 @@ struct fvm_ctx {
   double* aat;           // adjoint of the smoothed alpha
   double* atmp;          // between the two smoothing transposes
   double* aK;            // kAdjSlots coefficient slots of the two-pass transposes
+  double* apst[3];       // forward pressure of each stage (the density term)
   double adj_dt;         // dt of the step being adjoined
   // kernel timing with CUDA events (measurement aid, off by default)
   int prof;
@@ -281,7 +282,7 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
   size_t o_dt = pl.take(2 * sizeof(double));   // dt and 1/dt
   size_t o_lim = pl.take(sizeof(int));
   size_t o_ctl = pl.take((1 + kRecords) * sizeof(SolveCtl) + sizeof(int) + sizeof(unsigned long long));
-  constexpr int kAdjFields = 18;
+  constexpr int kAdjFields = 21;
   size_t o_adj[kAdjFields];
   size_t o_K = 0;
   if (p.adjoint) {
@@ -334,11 +335,13 @@ size_t plan_workspace(const fvm_params& p, fvm_ctx* c) {
       for (int q = 0; q < 3; ++q) c->aM[q] = a[13 + q];
       c->aat = a[16];
       c->atmp = a[17];
+      for (int q = 0; q < 3; ++q) c->apst[q] = a[18 + q];
       c->aK = (double*)(w + o_K);
     } else {
       c->aK = nullptr;
       for (int q = 0; q < 5; ++q) { c->aL[q] = nullptr; c->aE[q] = nullptr; }
       c->ap = c->apf = c->akap = c->aat = c->atmp = nullptr;
+      for (int q = 0; q < 3; ++q) c->apst[q] = nullptr;
       for (int q = 0; q < 3; ++q) c->aM[q] = nullptr;
     }
   }
@@ -1170,34 +1173,16 @@ double source_x(const fvm_ctx* c, long step_index, int q) {
 // X is the stage input.  kappa, as, tmp, us, b, beta0 and the adjoint
 // buffers serve as scratch; aE is overwritten.
 fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* const* lu,
-                         int* cyc, double* rel) {
+                         const double* pfw, int* cyc, double* rel) {
   cudaStream_t s = c->stream;
   const Geo& g = c->g;
   const long long N = g.N;
-  // 1. projection: with constant beta, P = I - beta G L^{-1} (-D) is
-  //    symmetric on the interior faces, so lus = P aE_u (wall faces zeroed
-  //    on both sides, as the forward zeroes them)
-  double* aEu[3] = {c->aE[0], c->aE[1], c->aE[2]};
-  double* lus[3] = {(double*)c->us[0], (double*)c->us[1], (double*)c->us[2]};
-  TIMED(c, FVM_K_ADJOINT, 1, launch_zero_wall_faces(g, aEu, s));
-  TIMED(c, FVM_K_DIV_RHS, 1, launch_div_rhs<double>(g, aEu, c->dt_dev, c->b, c->partial, s));
-  TIMED(c, FVM_K_MISC, 1, launch_sum_partials(c->partial, kRedBlocks, c->scal + 3, s));
-  TIMED(c, FVM_K_MISC, 1, launch_sub_mean(c->b, N, c->scal + 3, s));
+  const bool density = c->ph.rho[0] != c->ph.rho[1];
+  // 0. forward quantities of the stage input: face coefficients, curvature,
+  //    Marangoni vector, smoothed alpha and, with unequal densities, the
+  //    momentum predictor's force sum Phi = V + f_n + f_M per face
   double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};
   TIMED(c, FVM_K_BETA, 1, launch_beta<double, double>(g, c->ph, X[3], be[0], be[1], be[2], s));
-  TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->ap, N, s));
-  fvm_status st = solve_f64(c, c->ap, c->b, cyc, rel, true);
-  if (st && st != FVM_ENOCONV) return st;
-  fvm_status worst = st;
-  Fields<double> E;
-  for (int d = 0; d < 3; ++d) E.u[d] = aEu[d];
-  E.alpha = c->aE[3];
-  E.T = c->aE[4];
-  Fields<double> Y = E;
-  for (int d = 0; d < 3; ++d) Y.u[d] = lus[d];
-  TIMED(c, FVM_K_CORRECT, 1,
-        launch_correct<double, double>(g, E, Y, aEu, c->ap, be, c->dt_dev, 0.0, 1.0, s));
-  // 2. curvature and smoothed alpha of the stage input
   double* M[3] = {(double*)c->M[0], (double*)c->M[1], (double*)c->M[2]};
   const int passes = c->prm.smooth_passes;
   TIMED(c, FVM_K_INTERFACE, 1, launch_interface<double>(g, c->ph, c->tb, passes, X[3], X[4], nullptr,
@@ -1211,6 +1196,37 @@ fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* 
     TIMED(c, FVM_K_SMOOTH, 1, launch_smooth<double>(g, (const double*)c->tmp, (double*)c->as, s));
     at = (const double*)c->as;
   }
+  // scratch from the coefficient slots (free until the transposes below)
+  double* phi[3] = {c->aK, c->aK + N, c->aK + 2 * N};
+  double* ustar[3] = {c->aK + 3 * N, c->aK + 4 * N, c->aK + 5 * N};
+  double* wbeta[3] = {c->aK + 6 * N, c->aK + 7 * N, c->aK + 8 * N};
+  if (density) {
+    const double* Xc[5] = {X[0], X[1], X[2], X[3], X[4]};
+    Fields<double> Xf;
+    for (int d = 0; d < 3; ++d) Xf.u[d] = (double*)Xc[d];
+    Xf.alpha = (double*)Xc[3];
+    Xf.T = (double*)Xc[4];
+    Xf.c = nullptr;
+    TIMED(c, FVM_K_MOMENTUM, 1,
+          launch_momentum<double>(g, c->ph, c->tb, Xf, (double*)c->kappa, M[0], M[1], M[2],
+                                  ustar[0], ustar[1], ustar[2], c->dt_dev, s, phi));
+  }
+  // 1. projection: u = P u* with P = I + beta G L^+ D, so the adjoint of u*
+  //    is P^T aE_u = aE_u + G L^+ D (beta aE_u): the same solve on the
+  //    divergence of beta aE_u, then the plain gradient (wall faces zeroed on
+  //    both sides, as the forward zeroes them)
+  double* aEu[3] = {c->aE[0], c->aE[1], c->aE[2]};
+  double* lus[3] = {(double*)c->us[0], (double*)c->us[1], (double*)c->us[2]};
+  TIMED(c, FVM_K_ADJOINT, 1, launch_zero_wall_faces(g, aEu, s));
+  TIMED(c, FVM_K_ADJOINT, 1, launch_face_mul(g, be, aEu, wbeta, s));
+  TIMED(c, FVM_K_DIV_RHS, 1, launch_div_rhs<double>(g, wbeta, c->dt_dev, c->b, c->partial, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sum_partials(c->partial, kRedBlocks, c->scal + 3, s));
+  TIMED(c, FVM_K_MISC, 1, launch_sub_mean(c->b, N, c->scal + 3, s));
+  TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->ap, N, s));
+  fvm_status st = solve_f64(c, c->ap, c->b, cyc, rel, true);
+  if (st && st != FVM_ENOCONV) return st;
+  fvm_status worst = st;
+  TIMED(c, FVM_K_CORRECT, 1, launch_sub_grad(g, aEu, c->ap, c->dt_dev, lus, s));
   TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->akap, N, s));
   for (int d = 0; d < 3; ++d) TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->aM[d], N, s));
   TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->aat, N, s));
@@ -1243,7 +1259,11 @@ fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* 
     A.lam[q] = ph.lam[q];
     A.rcp[q] = ph.rcp[q];
   }
-  A.irho = 1.0 / ph.rho[0];
+  for (int d = 0; d < 3; ++d) {
+    A.beta[d] = be[d];
+    A.phi[d] = phi[d];
+  }
+  A.pfw = pfw;
   A.sigma0 = ph.sigma0;
   A.dsdT = ph.dsdT;
   A.T0 = ph.T0;
@@ -1254,6 +1274,7 @@ fvm_status adjoint_stage(fvm_ctx* c, const double* const* X, double xc, double* 
   A.yc = ph.q_y0;
   A.qpower = ph.q_power;
   for (int d = 0; d < 3; ++d) A.L[d] = ph.L[d];
+  if (density) TIMED(c, FVM_K_ADJOINT, 1, launch_adj_density(A, s));
   TIMED(c, FVM_K_ADJOINT, 8, launch_adj_scalars(A, s));
   TIMED(c, FVM_K_ADJOINT, 7, launch_adj_momentum(A, s));
   TIMED(c, FVM_K_ADJOINT, 8, launch_adj_interface(A, s));
@@ -1289,14 +1310,29 @@ fvm_status step_adjoint_impl(fvm_ctx* c, const fvm_state* st_n, long step_index,
   double rel = 0.0;
   fvm_status worst = FVM_OK;
   bool recomputed_on_device = false;
-  for (int q = 0; q < 2; ++q) {
+  // with unequal densities the third stage is recomputed as well (into the
+  // free adjoint buffers): every stage's forward pressure enters the adjoint
+  const bool density = c->ph.rho[0] != c->ph.rho[1];
+  Fields<double> Y2 = fields_of<double>(c->A);
+  for (int f = 0; f < 5; ++f) {
+    double* t = c->aL[f];
+    if (f < 3) Y2.u[f] = t;
+    else if (f == 3) Y2.alpha = t;
+    else Y2.T = t;
+  }
+  for (int q = 0; q < (density ? 3 : 2); ++q) {
     bool dev_side = false;
-    fvm_status r = stage<double>(c, q == 0 ? Sn : A, Sn, q == 0 ? A : B, c->apf, kRK[q][0],
-                                 kRK[q][1], source_x(c, step_index, q), q, &cyc, &rel, false,
-                                 &dev_side);
+    Fields<double> Xs = q == 0 ? Sn : (q == 1 ? A : B);
+    Fields<double> Ys = q == 0 ? A : (q == 1 ? B : Y2);
+    fvm_status r = stage<double>(c, Xs, Sn, Ys, c->apf, kRK[q][0], kRK[q][1],
+                                 source_x(c, step_index, q), q, &cyc, &rel, false, &dev_side);
     recomputed_on_device = recomputed_on_device || dev_side;
     if (r == FVM_ENOCONV) worst = r;
     else if (r) return r;
+    if (density) {
+      ce = cudaMemcpyAsync(c->apst[q], c->apf, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      if (ce != cudaSuccess) return set_err(c, FVM_ECUDA, cudaGetErrorString(ce));
+    }
   }
   const double* Xq[3][5] = {
       {(const double*)st_n->u, (const double*)st_n->v, (const double*)st_n->w,
@@ -1327,21 +1363,22 @@ fvm_status step_adjoint_impl(fvm_ctx* c, const fvm_state* st_n, long step_index,
       for (int f = 0; f < 5; ++f) TIMED(c, FVM_K_MISC, 1, launch_zero<double>(c->aL[f], N, s));
       lu = c->aL;
     }
-    fvm_status r = adjoint_stage(c, Xq[q], source_x(c, step_index, q), lu, &cyc, &rel);
+    fvm_status r = adjoint_stage(c, Xq[q], source_x(c, step_index, q), lu,
+                                 density ? c->apst[q] : nullptr, &cyc, &rel);
     if (r == FVM_ENOCONV) worst = r;
     else if (r) return r;
     for (int f = 0; f < 5; ++f) lamY[f] = c->aL[f];
   }
   TIMED(c, FVM_K_ADJOINT, 1, launch_zero_wall_faces(c->g, out, s));
   double th[2];
-  SolveCtl recs[2];
+  SolveCtl recs[3];
   ce = cudaMemcpyAsync(th, c->scal + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess && recomputed_on_device)
     ce = cudaMemcpyAsync(recs, c->rec, sizeof(recs), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) return set_err(c, FVM_ECUDA, cudaGetErrorString(ce));
   if (recomputed_on_device)
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < (density ? 3 : 2); ++q) {
       fvm_status r = record_status(c, recs[q]);
       if (r == FVM_EUNSTABLE) return r;
       if (r == FVM_ENOCONV) worst = r;
@@ -1365,9 +1402,10 @@ extern "C" fvm_status fvm_step_adjoint(fvm_ctx* ctx, const fvm_state* st_n, long
   if (!ctx->prm.adjoint) return set_err(ctx, FVM_EINVAL, "context created without adjoint = 1");
   if (ctx->mixed) return set_err(ctx, FVM_EUNSUPPORTED, "the adjoint is FP64 only");
   const fvm_params& p = ctx->prm;
-  if (p.rho[0] != p.rho[1] || p.mu[0] != p.mu[1] || p.cp[0] != p.cp[1] ||
-      p.lambda[0] != p.lambda[1])
-    return set_err(ctx, FVM_EUNSUPPORTED, "the adjoint needs equal phase properties");
+  if (p.mu[0] != p.mu[1] || p.lambda[0] != p.lambda[1] ||
+      p.rho[0] * p.cp[0] != p.rho[1] * p.cp[1])
+    return set_err(ctx, FVM_EUNSUPPORTED,
+                   "the adjoint needs equal viscosity, conductivity and rho c_p in both phases");
   if (!(dt > 0.0)) return set_err(ctx, FVM_EINVAL, "dt must be > 0");
   const void* a[5] = {lam_np1->u, lam_np1->v, lam_np1->w, lam_np1->alpha, lam_np1->T};
   const void* b[5] = {lam_n->u, lam_n->v, lam_n->w, lam_n->alpha, lam_n->T};

@@ -99,10 +99,11 @@ void launch_fct_ratios(const Geo& g, const Phys& ph, Fields<R> X, const double* 
 template <typename R>
 void launch_concentration(const Geo& g, const Phys& ph, Fields<R> X, Fields<R> Sn, Fields<R> Y,
                           const double* dt, double a, double b, cudaStream_t s);
+// phi (optional): the force sum V + f_n + f_M of every face before 1/rho_f
 template <typename R>
 void launch_momentum(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, const R* kappa,
                      const R* M0, const R* M1, const R* M2, R* us0, R* us1, R* us2,
-                     const double* dt, cudaStream_t s);
+                     const double* dt, cudaStream_t s, R* const* phi = nullptr);
 template <typename R>
 void launch_div_rhs(const Geo& g, R* const* us, const double* dt, double* b, double* partial,
                     cudaStream_t s);

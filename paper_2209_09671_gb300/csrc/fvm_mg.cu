@@ -376,13 +376,13 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, double* __rest
 // sweep (and within restriction and prolongation) the points are
 // independent, so the result equals that of the per-level kernels bit for bit.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A) {
-  __shared__ double sh[33];
-  const int last = A.nl - 1;
+__device__ void tail_body(const MGLevel<T>* Ls, int nl, double* r, double* d, double* Ad,
+                          double rtol, int maxit, int pre, int post, double* sh) {
+  const int last = nl - 1;
   for (int l = 0; l < last; ++l) {
-    const MGLevel<T>& L = A.L[l];
+    const MGLevel<T>& L = Ls[l];
     const Geo& g = L.geo;
-    for (int it = 0; it < A.pre; ++it)
+    for (int it = 0; it < pre; ++it)
       for (int col = 0; col < 2; ++col) {
         for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) {
           int i, j, k;
@@ -391,18 +391,18 @@ __global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A) {
         }
         __syncthreads();
       }
-    for (int cc = threadIdx.x; cc < (int)A.L[l + 1].geo.N; cc += blockDim.x)
-      restrict_point(L, A.L[l + 1], cc);
+    for (int cc = threadIdx.x; cc < (int)Ls[l + 1].geo.N; cc += blockDim.x)
+      restrict_point(L, Ls[l + 1], cc);
     __syncthreads();
   }
-  coarse_cg_block(A.L[last], A.r, A.d, A.Ad, A.rtol, A.maxit, sh);
+  coarse_cg_block(Ls[last], r, d, Ad, rtol, maxit, sh);
   __syncthreads();
   for (int l = last - 1; l >= 0; --l) {
-    const MGLevel<T>& L = A.L[l];
+    const MGLevel<T>& L = Ls[l];
     const Geo& g = L.geo;
-    for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) prolong_point(L, A.L[l + 1], c);
+    for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) prolong_point(L, Ls[l + 1], c);
     __syncthreads();
-    for (int it = 0; it < A.post; ++it)
+    for (int it = 0; it < post; ++it)
       for (int col = 0; col < 2; ++col) {
         for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) {
           int i, j, k;
@@ -412,6 +412,12 @@ __global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A) {
         __syncthreads();
       }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A) {
+  __shared__ double sh[33];
+  tail_body(A.L, A.nl, A.r, A.d, A.Ad, A.rtol, A.maxit, A.pre, A.post, sh);
 }
 
 template <typename T>

@@ -769,7 +769,8 @@ template <int D, typename R>
 __device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>& ph, const TBC& tb,
                                                    const Fields<R>& X, const R* __restrict__ kappa,
                                                    const R* __restrict__ MD, bool in,
-                                                   MomShared<R>& S, R* __restrict__ us, R dt) {
+                                                   MomShared<R>& S, R* __restrict__ us, R dt,
+                                                   R* __restrict__ phi) {
   constexpr int t1 = Tang<D>::t1, t2 = Tang<D>::t2;
   const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
   const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
@@ -812,6 +813,7 @@ __device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>&
     const int c = (k * ny + j) * nx + i;
     if (g.bc[D] == WALL && gi[D] == 0) {
       us[c] = R(0);
+      if (phi) phi[c] = R(0);
     } else {
       const R ih = ph.ih;
       int ci = tx, cj = ty, ck = tz;
@@ -844,6 +846,7 @@ __device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>&
       const R fn = -sig_f * kap_f * jump;
       const R fM = R(0.5) * (g_even(MD, g, in, a, b, cc) + MD[c]);
       us[c] = S.u[D][Tile<3>::at(tx, ty, tz)] + dt * (A + (V + fn + fM) / rho_f + ph.g[D]);
+      if (phi) phi[c] = V + fn + fM;   // the force sum before 1/rho_f (the adjoint's density term)
     }
   }
   __syncthreads();
@@ -854,7 +857,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 1)
     k_momentum(Geo g, PhysR<R> ph, TBC tb, Fields<R> X, const R* __restrict__ kappa,
                const R* __restrict__ M0, const R* __restrict__ M1, const R* __restrict__ M2,
                R* __restrict__ us0, R* __restrict__ us1, R* __restrict__ us2,
-               const double* __restrict__ dtp) {
+               const double* __restrict__ dtp, R* __restrict__ ph0, R* __restrict__ ph1,
+               R* __restrict__ ph2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MomShared<R>& S = *reinterpret_cast<MomShared<R>*>(smem_raw);
   stage<3, F_VEL, 0>(S.u[0], X.u[0], g, tb);
@@ -866,22 +870,23 @@ __global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 1)
   __syncthreads();
   const R dt = (R)dtp[0];
   const bool in = tile_interior(g, 3);
-  momentum_component<0>(g, ph, tb, X, kappa, M0, in, S, us0, dt);
-  momentum_component<1>(g, ph, tb, X, kappa, M1, in, S, us1, dt);
-  momentum_component<2>(g, ph, tb, X, kappa, M2, in, S, us2, dt);
+  momentum_component<0>(g, ph, tb, X, kappa, M0, in, S, us0, dt, ph0);
+  momentum_component<1>(g, ph, tb, X, kappa, M1, in, S, us1, dt, ph1);
+  momentum_component<2>(g, ph, tb, X, kappa, M2, in, S, us2, dt, ph2);
 }
 
 template <typename R>
 void launch_momentum(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, const R* kappa,
                      const R* M0, const R* M1, const R* M2, R* us0, R* us1, R* us2,
-                     const double* dt, cudaStream_t s) {
+                     const double* dt, cudaStream_t s, R* const* phi) {
   const int smem = (int)sizeof(MomShared<R>);
   cudaFuncSetAttribute(k_momentum<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // float tiles (71 KB) fit three CTAs per SM when the L1/shared split favours shared memory
   cudaFuncSetAttribute(k_momentum<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   k_momentum<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
-      g, make_physr<R>(ph, g), tb, X, kappa, M0, M1, M2, us0, us1, us2, dt);
+      g, make_physr<R>(ph, g), tb, X, kappa, M0, M1, M2, us0, us1, us2, dt,
+      phi ? phi[0] : nullptr, phi ? phi[1] : nullptr, phi ? phi[2] : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1158,7 +1163,7 @@ void launch_diagnostics(const Geo& g, const Phys& ph, Fields<R> X, const double*
                                      cudaStream_t);                                              \
   template void launch_momentum<R>(const Geo&, const Phys&, const TBC&, Fields<R>, const R*,     \
                                    const R*, const R*, const R*, R*, R*, R*, const double*,      \
-                                   cudaStream_t);                                                \
+                                   cudaStream_t, R* const*);                                     \
   template void launch_div_rhs<R>(const Geo&, R* const*, const double*, double*, double*,        \
                                   cudaStream_t);                                                 \
   template void launch_dt_reduce<R>(const Geo&, const Phys&, Fields<R>, unsigned long long*,     \

@@ -19,9 +19,14 @@ FIELDS = A.FIELDS
 TOL = 1e-9
 
 
-def _case(shape, passes=2, bc=None, vel=0.02, ripple=0.6):
+def _case(shape, passes=2, bc=None, vel=0.02, ripple=0.6, density=1.0):
+    """The channel physics; density > 1 makes the alpha = 1 phase that much
+    denser with its heat capacity per mass lowered in proportion (equal
+    rho c_p, viscosity and conductivity: the setting the adjoint supports)."""
     p, s = cases.adjoint_channel(nx=shape[0], ny=shape[1], nz=shape[2], ripple=ripple)
     p = p.replace(mg_rtol=1e-13, adjoint=1, smooth_passes=passes, precision=cases.F64)
+    if density != 1.0:
+        p = p.replace(rho=(p.rho[0], p.rho[0] * density), cp=(p.cp[0], p.cp[0] / density))
     if bc is not None:
         p = p.replace(bc=bc)
     for i, k in enumerate(("u", "v", "w")):
@@ -30,17 +35,19 @@ def _case(shape, passes=2, bc=None, vel=0.02, ripple=0.6):
     return p, s
 
 
-@pytest.mark.parametrize("shape,passes,bc", [
-    ((16, 16, 8), 2, None),
-    ((32, 32, 16), 2, None),
-    ((40, 24, 12), 2, None),          # ragged against the 32 x 4 x 4 tiles
-    ((16, 16, 8), 1, None),
-    ((16, 16, 8), 0, None),
-    ((16, 12, 8), 2, (1, 0, 1)),      # a second wall axis (x)
+@pytest.mark.parametrize("shape,passes,bc,density", [
+    ((16, 16, 8), 2, None, 1.0),
+    ((32, 32, 16), 2, None, 1.0),
+    ((40, 24, 12), 2, None, 1.0),          # ragged against the 32 x 4 x 4 tiles
+    ((16, 16, 8), 1, None, 1.0),
+    ((16, 16, 8), 0, None, 1.0),
+    ((16, 12, 8), 2, (1, 0, 1), 1.0),      # a second wall axis (x)
+    ((16, 16, 8), 2, None, 10.0),          # unequal densities: the d L / d alpha terms
+    ((20, 12, 8), 2, (1, 0, 1), 100.0),
 ])
-def test_step_adjoint_matches_oracle(shape, passes, bc):
+def test_step_adjoint_matches_oracle(shape, passes, bc, density):
     P = need_gpu()
-    p, s = _case(shape, passes, bc)
+    p, s = _case(shape, passes, bc, density=density)
     dt = 0.2 * p.h * p.h
     lam = {k: cases.uniform(20 + i, p.shape, -1, 1) for i, k in enumerate(FIELDS)}
     ref, dth_ref = A.step_vjp(s, p, 2, dt, lam, rtol=1e-13)
@@ -85,13 +92,15 @@ def _rollout_J(P, p, s, dts, state_delta=None, eps=0.0):
     return J
 
 
-def test_rollout_gradient_matches_central_differences():
+@pytest.mark.parametrize("density", [1.0, 10.0])
+def test_rollout_gradient_matches_central_differences(density):
     """Four steps of the 32 x 32 x 16 channel with a flat interface, starting
     at rest: dJ/dtheta and the directional derivative along a smooth state
-    perturbation agree with central differences of the GPU forward to 1e-6."""
+    perturbation agree with central differences of the GPU forward to 1e-6
+    (equal densities, and a ten times denser lower layer)."""
     P = need_gpu()
     from paper_2209_09671_gb300 import adjoint as ADJ
-    p, s = _case((32, 32, 16), vel=0.0, ripple=0.0)
+    p, s = _case((32, 32, 16), vel=0.0, ripple=0.0, density=density)
     dts = [0.25 * p.h * p.h] * 4
     x, y, z = cases.cell_centres(p)
     T0 = torch.tensor(s["T"], device="cuda")
@@ -157,12 +166,13 @@ def test_adjoint_argument_errors():
         solver.fvm_step_adjoint(dev, 0, dt, lam)
     assert e.value.status == fvm.FVM_EINVAL
     solver.close()
-    # unequal densities
-    solver = P.Solver(p.replace(rho=(1.0, 2.0)))
-    with pytest.raises(fvm.FvmError) as e:
-        solver.fvm_step_adjoint(dev, 0, dt, lam)
-    assert e.value.status == fvm.FVM_EUNSUPPORTED
-    solver.close()
+    # unequal viscosities, or unequal densities with unequal rho c_p
+    for q in (p.replace(mu=(1.0, 2.0)), p.replace(rho=(1.0, 2.0))):
+        solver = P.Solver(q)
+        with pytest.raises(fvm.FvmError) as e:
+            solver.fvm_step_adjoint(dev, 0, dt, lam)
+        assert e.value.status == fvm.FVM_EUNSUPPORTED
+        solver.close()
     solver = P.Solver(p)
     # dt must be given
     with pytest.raises(fvm.FvmError) as e:
