@@ -359,13 +359,44 @@ __device__ void coarse_cg_block(const MGLevel<T>& L, double* __restrict__ r,
   for (int c = threadIdx.x; c < N; c += blockDim.x) L.x[c] = (T)(x[c] - xm);
 }
 
+// The coarsest-level CG of a single CTA is bound by the latency of every
+// iteration's dependent phases (operator, two reductions, updates); when the
+// level is small its vectors and face coefficients are kept in shared
+// memory instead of global memory (the same arithmetic in the same order).
+constexpr int kCgSmemCells = 640;
+struct CgSmem {
+  double v[4][kCgSmemCells];   // r, d, Ad, x
+  double beta[3][kCgSmemCells];
+};
+
+template <typename T>
+__device__ void coarse_cg_dispatch(const MGLevel<T>& L, double* r, double* dd, double* Ad,
+                                   double rtol, int maxit, double* sh, CgSmem& cs) {
+  const int N = (int)L.geo.N;
+  if (N > kCgSmemCells || sizeof(T) > sizeof(double)) {
+    coarse_cg_block(L, r, dd, Ad, rtol, maxit, sh);
+    return;
+  }
+  // face coefficients staged in the level's precision T; the operator then
+  // reads them through a copy of the level whose beta points to them
+  T* bs = reinterpret_cast<T*>(&cs.beta[0][0]);
+  MGLevel<T> S = L;
+  for (int q = 0; q < 3; ++q) {
+    S.beta[q] = bs + q * kCgSmemCells;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) S.beta[q][c] = L.beta[q][c];
+  }
+  __syncthreads();
+  coarse_cg_block(S, cs.v[0], cs.v[1], cs.v[2], rtol, maxit, sh);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, double* __restrict__ r,
                                                     double* __restrict__ dd,
                                                     double* __restrict__ Ad, double rtol,
                                                     int maxit) {
   __shared__ double sh[33];
-  coarse_cg_block(L, r, dd, Ad, rtol, maxit, sh);
+  __shared__ CgSmem cs;
+  coarse_cg_dispatch(L, r, dd, Ad, rtol, maxit, sh, cs);
 }
 
 // The coarse tail of a V-cycle in one CTA: levels small enough that a kernel
@@ -377,7 +408,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, double* __rest
 // independent, so the result equals that of the per-level kernels bit for bit.
 template <typename T>
 __device__ void tail_body(const MGLevel<T>* Ls, int nl, double* r, double* d, double* Ad,
-                          double rtol, int maxit, int pre, int post, double* sh) {
+                          double rtol, int maxit, int pre, int post, double* sh, CgSmem& cs) {
   const int last = nl - 1;
   for (int l = 0; l < last; ++l) {
     const MGLevel<T>& L = Ls[l];
@@ -395,7 +426,7 @@ __device__ void tail_body(const MGLevel<T>* Ls, int nl, double* r, double* d, do
       restrict_point(L, Ls[l + 1], cc);
     __syncthreads();
   }
-  coarse_cg_block(Ls[last], r, d, Ad, rtol, maxit, sh);
+  coarse_cg_dispatch(Ls[last], r, d, Ad, rtol, maxit, sh, cs);
   __syncthreads();
   for (int l = last - 1; l >= 0; --l) {
     const MGLevel<T>& L = Ls[l];
@@ -417,7 +448,8 @@ __device__ void tail_body(const MGLevel<T>* Ls, int nl, double* r, double* d, do
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A) {
   __shared__ double sh[33];
-  tail_body(A.L, A.nl, A.r, A.d, A.Ad, A.rtol, A.maxit, A.pre, A.post, sh);
+  __shared__ CgSmem cs;
+  tail_body(A.L, A.nl, A.r, A.d, A.Ad, A.rtol, A.maxit, A.pre, A.post, sh, cs);
 }
 
 template <typename T>
