@@ -106,6 +106,8 @@ def parse():
                     help="grid of the melt-pool surrogate (overrides --n), e.g. 512 512 256")
     ap.add_argument("--mg-pre", type=int, default=None, help="pre-smoothing sweeps (default 2)")
     ap.add_argument("--mg-post", type=int, default=None, help="post-smoothing sweeps (default 2)")
+    ap.add_argument("--mg-coarse", type=int, default=None,
+                    help="sweeps before and after the correction on the coarse levels (default 3)")
     ap.add_argument("--mg-levels", type=int, default=None,
                     help="cap on the multigrid hierarchy depth (default: the workload's)")
     ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
@@ -723,6 +725,8 @@ def run_ours(args, rank, world, local_rank):
         p = p.replace(mg_pre=args.mg_pre)
     if args.mg_post is not None:
         p = p.replace(mg_post=args.mg_post)
+    if args.mg_coarse is not None:
+        p = p.replace(mg_coarse_sweeps=args.mg_coarse)
     with torch.cuda.stream(stream):
         solver = P.Solver(p, device=dev, stream=stream)
         state = P.to_device(s0, True, dev)
@@ -902,7 +906,7 @@ def run_ours(args, rank, world, local_rank):
                    "grid": list(shape), "precision": "mixed", "mg_rtol": p.mg_rtol,
                    "mg_levels": p.mg_levels,
                    "mx_inner_cycles": p.mx_inner_cycles, "mg_pre": p.mg_pre,
-                   "mg_post": p.mg_post,
+                   "mg_post": p.mg_post, "mg_coarse_sweeps": p.mg_coarse_sweeps,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": f"inputs larger than L2 (state {N * 28 / 2**20:.0f} MiB)"},
         "roofline": roof,

@@ -120,6 +120,7 @@ class Params:
     diff_c: tuple = (0.0, 0.0)                          # diffusivity of c per phase
     weno_scale_c: float = 1.0                           # WENO5 eps scale of c
     alpha_scheme: int = 0                               # 0 WENO5, 1 bounded (FCT blend)
+    mg_coarse_sweeps: int = 3                           # pre/post sweeps below the finest level
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -110,6 +110,11 @@ typedef struct {
    * keeps every stage's alpha within [0, 1] (the paper's Sec. V-A mixes
    * first-order bounded and high-order WENO schemes); not with adjoint = 1 */
   int alpha_scheme;
+  /* red-black sweeps before and after the coarse correction on every level
+   * below the finest (0: mg_pre and mg_post there too); the coarse levels are
+   * small and cache-resident, and three sweeps there halve the V-cycle's
+   * convergence factor on the melt-pool operator (0.15 -> 0.08) */
+  int mg_coarse_sweeps;
 } fvm_params;
 
 /* Caller-owned device fields of one state. u, v, w, alpha, T (and c): double

@@ -771,14 +771,26 @@ def coarse_cg(b, lev, rtol, maxit):
     return x - x.mean()
 
 
+def sweeps(prm, l):
+    """Pre- and post-smoothing sweeps of level l: mg_pre, mg_post on the
+    finest level; mg_coarse_sweeps each on the coarser ones (0: the finest
+    level's counts)."""
+    c = int(getattr(prm, "mg_coarse_sweeps", 0))
+    if l == 0 or c == 0:
+        return prm.mg_pre, prm.mg_post
+    return c, c
+
+
 def vcycle(levels, l, x, b, prm):
     """V(pre, post) cycle: red-black GS (red first) before, residual
     restricted by the mean of the children, piecewise-constant prolongation,
-    black-red GS after; CG on the coarsest level."""
+    black-red GS after; CG on the coarsest level.  The coarse levels take
+    their own sweep count (``sweeps``)."""
     lev = levels[l]
     if l == len(levels) - 1:
         return coarse_cg(b, lev, prm.coarse_rtol, prm.coarse_maxit)
-    for _ in range(prm.mg_pre):
+    pre, post = sweeps(prm, l)
+    for _ in range(pre):
         x = gs_colour(x, b, lev, 0)
         x = gs_colour(x, b, lev, 1)
     r = b - apply_L(x, lev)
@@ -786,7 +798,7 @@ def vcycle(levels, l, x, b, prm):
     bc_ = restrict_mean(r, f)
     ec = vcycle(levels, l + 1, torch.zeros_like(bc_), bc_, prm)
     x = x + ec.repeat_interleave(f[2], 0).repeat_interleave(f[1], 1).repeat_interleave(f[0], 2)
-    for _ in range(prm.mg_post):
+    for _ in range(post):
         x = gs_colour(x, b, lev, 1)
         x = gs_colour(x, b, lev, 0)
     return x

@@ -115,6 +115,7 @@ const char* check_params(const fvm_params* p) {
   if (p->adjoint && p->precision != FVM_F64) return "the adjoint needs precision F64";
   if (p->concentration != 0 && p->concentration != 1) return "concentration must be 0 or 1";
   if (p->alpha_scheme != 0 && p->alpha_scheme != 1) return "alpha_scheme must be 0 or 1";
+  if (p->mg_coarse_sweeps < 0) return "mg_coarse_sweeps must be >= 0";
   if (p->alpha_scheme == 1 && p->adjoint) return "the adjoint does not support the bounded scheme";
   if (p->concentration) {
     if (!(p->diff_c[0] >= 0.0) || !(p->diff_c[1] >= 0.0)) return "diff_c must be >= 0";
@@ -413,6 +414,14 @@ void smooth(fvm_ctx* c, MGLevel<T>& L, int l, int iters, int first) {
   }
 }
 
+// sweeps on the levels below the finest
+int coarse_pre(const fvm_ctx* c) {
+  return c->prm.mg_coarse_sweeps > 0 ? c->prm.mg_coarse_sweeps : c->prm.mg_pre;
+}
+int coarse_post(const fvm_ctx* c) {
+  return c->prm.mg_coarse_sweeps > 0 ? c->prm.mg_coarse_sweeps : c->prm.mg_post;
+}
+
 // first level of the one-CTA coarse tail (at most kTailCells cells, not the
 // finest, at least one level above the coarsest), or -1
 int tail_start(const fvm_ctx* c) {
@@ -439,8 +448,8 @@ void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
     A.Ad = (double*)c->cg[2];
     A.rtol = coarse_rtol;
     A.maxit = c->prm.coarse_maxit;
-    A.pre = c->prm.mg_pre;
-    A.post = c->prm.mg_post;
+    A.pre = coarse_pre(c);
+    A.post = coarse_post(c);
     TIMED(c, FVM_K_COARSE_TAIL, 1, launch_coarse_tail<T>(A, s));
     return;
   }
@@ -449,13 +458,13 @@ void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
                                                    coarse_rtol, c->prm.coarse_maxit, s));
     return;
   }
-  smooth<T>(c, Ls[l], l, c->prm.mg_pre, 0);
+  smooth<T>(c, Ls[l], l, l == 0 ? c->prm.mg_pre : coarse_pre(c), 0);
   TIMED(c, l == 0 ? FVM_K_RESTRICT_FINE : FVM_K_RESTRICT_COARSE, 1,
         launch_residual_restrict<T>(Ls[l], Ls[l + 1], s));
   vcycle<T>(c, Ls, l + 1, coarse_rtol);
   TIMED(c, l == 0 ? FVM_K_PROLONG_FINE : FVM_K_PROLONG_COARSE, 1,
         launch_prolong<T>(Ls[l], Ls[l + 1], s));
-  smooth<T>(c, Ls[l], l, c->prm.mg_post, 1);
+  smooth<T>(c, Ls[l], l, l == 0 ? c->prm.mg_post : coarse_post(c), 1);
 }
 
 // F64: L p = b (b mean-free, double), beta0 already computed

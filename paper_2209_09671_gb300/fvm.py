@@ -48,6 +48,7 @@ class fvm_params(ctypes.Structure):
         ("diff_c", ctypes.c_double * 2),
         ("weno_scale_c", ctypes.c_double),
         ("alpha_scheme", ctypes.c_int),
+        ("mg_coarse_sweeps", ctypes.c_int),
     ]
 
 
@@ -167,6 +168,7 @@ def make_params(p) -> fvm_params:
     c.diff_c[:] = [float(v) for v in getattr(p, "diff_c", (0.0, 0.0))]
     c.weno_scale_c = float(getattr(p, "weno_scale_c", 1.0))
     c.alpha_scheme = int(getattr(p, "alpha_scheme", 0))
+    c.mg_coarse_sweeps = int(getattr(p, "mg_coarse_sweeps", 0))
     return c
 
 

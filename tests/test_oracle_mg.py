@@ -137,3 +137,26 @@ def test_convergence_factor_reasonable():
     x, cyc, rel = O.poisson_solve(alpha, b, np.zeros(p.shape), p)
     assert rel <= 1e-10
     assert cyc <= 17
+
+
+def test_coarse_level_sweeps_halve_the_convergence_factor():
+    """Three red-black sweeps before and after the correction on every level
+    below the finest (the default) against the finest level's two: on the
+    melt-pool operator (flat interface, density ratio 7900) the asymptotic
+    residual reduction per V-cycle goes from ~0.14 to ~0.08; the solution is
+    the same (both converge to the direct solve of the other tests)."""
+    p, s = cases.melt_pool(32, 32, 32, precision=cases.F64)
+    grid = O.Grid(p)
+    levels = O.build_hierarchy(O.fine_beta(torch.tensor(s["alpha"]), p, grid), grid, 16)
+    b = torch.tensor(cases.uniform(3, p.shape, -1, 1))
+    b = b - b.mean()
+    factors = {}
+    for cs in (0, 3):
+        q = p.replace(mg_coarse_sweeps=cs)
+        x = torch.zeros_like(b)
+        rs = []
+        for _ in range(8):
+            x = O.vcycle(levels, 0, x, b, q)
+            rs.append(((b - O.apply_L(x, levels[0])).norm() / b.norm()).item())
+        factors[cs] = rs[-1] / rs[-2]
+    assert factors[0] > 0.12 and factors[3] < 0.1, factors
