@@ -16,13 +16,16 @@
 //   k_dt_reduce   maxima for the time-step limits; k_dt_final combines them
 //   k_diagnostics volume / mass sums, max |D u| dt, NaN flag
 //
-// Layout of the work: a CTA owns a kBX x kBY x kBZ tile of cells on a 3D grid.
-// Every face flux (and every edge flux of the momentum control volumes) is
-// evaluated once, by the thread owning the face, and exchanged through shared
-// memory; the threads on the high (or low) side of the tile evaluate the one
-// extra layer the divergence needs.  Tiles whose stencil reach (3 cells)
-// stays inside the domain take loads without boundary handling; the others
-// go through the wrap/mirror loaders.
+// Layout of the work: k_interface, k_scalars and k_momentum march along z: a
+// CTA of kZX x kZY threads owns one (x, y) column of cells per thread and a
+// run of planes; each plane of a field is staged once in shared memory with
+// its x-y halo (copied asynchronously one step ahead), the z stencils come
+// from rings of planes or per-thread register windows, and every face flux
+// (and every edge flux of the momentum control volumes) is evaluated once.
+// The other stage kernels (concentration, flux-corrected ratios, smoothing)
+// own a kBX x kBY x kBZ tile of cells with a halo staged in shared memory.
+// Points whose stored value is what the boundary rule gives are read
+// directly; ghost points go through the wrap/mirror loaders.
 #include "fvm_device.cuh"
 
 namespace fvm {
@@ -197,201 +200,378 @@ __device__ __forceinline__ int tsel(int tx, int ty, int tz) {
 }
 
 // ---------------------------------------------------------------------------
-// interface geometry: two smoothing passes, face normals, curvature and the
-// Marangoni vector in one kernel (the smoothed alpha never leaves the SM)
-template <typename R>
-struct IfaceShared {
-  R a[Tile<3>::N];          // alpha
-  R s1[Tile<2>::N];         // after the first [1,2,1]/4 pass
-  R s2[Tile<1>::N];         // smoothed alpha
-  R T[Tile<1>::N];
-  R c[Tile<1>::N];          // concentration (when transported)
-  R nx[kBZ][kBY][kBX + 1];  // face normals
-  R ny[kBZ][kBY + 1][kBX];
-  R nz[kBZ + 1][kBY][kBX];
+// z-marching layout shared by the stage kernels: a
+// CTA of kZX x kZY threads owns one (x, y) column of cells per thread and
+// walks a run of planes upward.  Fields are staged one plane at a time in
+// shared memory with the x-y halo the stencil needs; what the z-direction
+// stencil needs stays in rings of planes (or in each thread's registers), so
+// the z halo is read once per column run rather than once per tile.
+constexpr int kZX = 32, kZY = 8;
+constexpr int kZT = kZX * kZY;
+
+template <int H>
+struct Plane {
+  static constexpr int PX = kZX + 2 * H, PY = kZY + 2 * H, N = PX * PY;
+  static __device__ __forceinline__ int at(int lx, int ly) { return (ly + H) * PX + lx + H; }
 };
 
-// one [1,2,1]/4 tensor pass from a tile of halo HI onto the tile of halo HO
-template <int HI, int HO, typename R>
-__device__ __forceinline__ void smooth_pass(const Geo& g, const R* __restrict__ in,
-                                            R* __restrict__ out) {
-  const bool sx = g.n[0] > 1, sy = g.n[1] > 1, sz = g.n[2] > 1;
-  constexpr int SX = Tile<HO>::SX, SY = Tile<HO>::SY, SZ = Tile<HO>::SZ;
-  for (int row = threadIdx.y + kBY * threadIdx.z; row < SY * SZ; row += kBY * kBZ) {
-    const int ly = row % SY - HO, lz = row / SY - HO;
-    for (int ex = threadIdx.x; ex < SX; ex += kBX) {
-      const int lx = ex - HO;
-      R acc = 0;
+static inline dim3 zmarch_grid(const Geo& g, int kz) {
+  return dim3((unsigned)((g.n[0] + kZX - 1) / kZX), (unsigned)((g.n[1] + kZY - 1) / kZY),
+              (unsigned)((g.n[2] + kz - 1) / kz));
+}
+
+// the CTA's columns and their x-y reach H stay inside the domain
+__device__ __forceinline__ bool zcols_interior(const Geo& g, int H) {
+  const int x0 = blockIdx.x * kZX, y0 = blockIdx.y * kZY;
+  return x0 - H >= 0 && x0 + kZX - 1 + H < g.n[0] && y0 - H >= 0 && y0 + kZY - 1 + H < g.n[1];
+}
+
+// direct loads of plane k are valid in an interior run of columns: a cell
+// plane inside the domain, a plane of z-faces strictly inside it (the wall
+// faces take the boundary rule)
+template <int KIND, int C>
+__device__ __forceinline__ bool plane_direct(const Geo& g, bool in, int k) {
+  return in && k >= ((KIND == F_VEL && C == 2) ? 1 : 0) && k < g.n[2];
+}
+
+// a point of plane k whose stored value is the value the boundary rule gives
+template <int KIND, int C>
+__device__ __forceinline__ bool point_direct(const Geo& g, int i, int j, int k) {
+  const bool vel = KIND == F_VEL;
+  return k >= ((vel && C == 2) ? 1 : 0) && k < g.n[2] && i >= ((vel && C == 0) ? 1 : 0) &&
+         i < g.n[0] && j >= ((vel && C == 1) ? 1 : 0) && j < g.n[1];
+}
+
+template <int KIND, int C, typename R>
+__device__ __forceinline__ R ld_rule(const R* __restrict__ a, const Geo& g, const TBC& tb, int i,
+                                     int j, int k) {
+  if (KIND == F_EVEN) return ld_even(a, g, i, j, k);
+  if (KIND == F_VEL) return ld_vel<C>(a, g, i, j, k);
+  return ld_T(a, g, tb, i, j, k);
+}
+
+// stage plane k of a field with an x-y halo of H (ghost planes k < 0 or
+// k >= nz through the boundary rules); points more than H cells outside the
+// domain (ragged tiles) are never read and hold 0
+template <int H, int KIND, int C = 0, typename R>
+__device__ __forceinline__ void stage_plane(R* __restrict__ s, const R* __restrict__ a,
+                                            const Geo& g, const TBC& tb, bool in, int k) {
+  using P = Plane<H>;
+  const int x0 = blockIdx.x * kZX - H, y0 = blockIdx.y * kZY - H;
+  const int nx = g.n[0], ny = g.n[1];
+  if (plane_direct<KIND, C>(g, in, k)) {
+    const R* __restrict__ ak = a + ((k * ny + y0) * nx + x0);
+    for (int ly = threadIdx.y; ly < P::PY; ly += kZY) {
 #pragma unroll
-      for (int dz = -1; dz <= 1; ++dz) {
-        if (!sz && dz != 0) continue;
-        const R wz = sz ? (dz == 0 ? R(0.5) : R(0.25)) : R(1);
-        R accy = 0;
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-          if (!sy && dy != 0) continue;
-          const R wy = sy ? (dy == 0 ? R(0.5) : R(0.25)) : R(1);
-          R accx = 0;
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) {
-            if (!sx && dx != 0) continue;
-            const R wx = sx ? (dx == 0 ? R(0.5) : R(0.25)) : R(1);
-            accx += wx * in[Tile<HI>::at(lx + dx, ly + dy, lz + dz)];
-          }
-          accy += wy * accx;
-        }
-        acc += wz * accy;
-      }
-      out[row * SX + ex] = acc;
+      for (int lx = threadIdx.x; lx < P::PX; lx += kZX) s[ly * P::PX + lx] = __ldg(ak + ly * nx + lx);
+    }
+    return;
+  }
+  for (int ly = threadIdx.y; ly < P::PY; ly += kZY) {
+    const int j = y0 + ly;
+    for (int lx = threadIdx.x; lx < P::PX; lx += kZX) {
+      const int i = x0 + lx;
+      R v;
+      if (i > nx - 1 + H || j > ny - 1 + H) v = R(0);
+      else if (point_direct<KIND, C>(g, i, j, k)) v = __ldg(a + ((k * ny + j) * nx + i));
+      else v = ld_rule<KIND, C>(a, g, tb, i, j, k);
+      s[ly * P::PX + lx] = v;
     }
   }
 }
 
-template <int HI, int HO, typename R>
-__device__ __forceinline__ void copy_tile(const R* __restrict__ in, R* __restrict__ out) {
-  constexpr int SX = Tile<HO>::SX, SY = Tile<HO>::SY, SZ = Tile<HO>::SZ;
-  for (int row = threadIdx.y + kBY * threadIdx.z; row < SY * SZ; row += kBY * kBZ) {
-    const int ly = row % SY - HO, lz = row / SY - HO;
-    for (int ex = threadIdx.x; ex < SX; ex += kBX)
-      out[row * SX + ex] = in[Tile<HI>::at(ex - HO, ly, lz)];
+// asynchronous staging of a plane: in an interior run of columns each point
+// is one cp.async copy from global to shared memory (4 or 8 bytes), so that
+// the next plane is in flight while the current one is used; near the
+// boundary the points go through the loaders and are stored directly.  The
+// consumer waits with cp_async_wait_all() followed by __syncthreads().
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* smem, const R* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(R) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <int H, int KIND, int C = 0, typename R>
+__device__ __forceinline__ void plane_async(R* __restrict__ s, const R* __restrict__ a,
+                                            const Geo& g, const TBC& tb, bool in, int k) {
+  using P = Plane<H>;
+  const int x0 = blockIdx.x * kZX - H, y0 = blockIdx.y * kZY - H;
+  const int nx = g.n[0], ny = g.n[1];
+  if (plane_direct<KIND, C>(g, in, k)) {
+    const R* __restrict__ ak = a + ((k * ny + y0) * nx + x0);
+    for (int ly = threadIdx.y; ly < P::PY; ly += kZY) {
+#pragma unroll
+      for (int lx = threadIdx.x; lx < P::PX; lx += kZX) cp_async_elem(s + ly * P::PX + lx, ak + ly * nx + lx);
+    }
+    return;
+  }
+  for (int ly = threadIdx.y; ly < P::PY; ly += kZY) {
+    const int j = y0 + ly;
+    for (int lx = threadIdx.x; lx < P::PX; lx += kZX) {
+      const int i = x0 + lx;
+      R* d = s + ly * P::PX + lx;
+      if (i > nx - 1 + H || j > ny - 1 + H) *d = R(0);
+      else if (point_direct<KIND, C>(g, i, j, k)) cp_async_elem(d, a + ((k * ny + j) * nx + i));
+      else *d = ld_rule<KIND, C>(a, g, tb, i, j, k);
+    }
   }
 }
 
-// n_D on the low D-face of local cell (lx,ly,lz), from the smoothed alpha:
-// grad / (|grad| + eps_n) with the normal derivative across the face and each
-// tangential derivative the mean of the two cells' central differences
+// ---------------------------------------------------------------------------
+// interface geometry: smoothed alpha, face normals, curvature and the
+// Marangoni vector in one kernel (the smoothed alpha never leaves the SM).
+// K passes of the [1,2,1]/4 filter along an axis are one binomial filter of
+// 2K+1 taps ([1,4,6,4,1]/16 for K = 2), and the passes along different axes
+// commute, so the smoothing is applied as one 5-tap pass per axis: x and y
+// on each staged plane, z across a ring of x-y-smoothed planes.
+constexpr int kZKI = 32;   // planes per CTA
+
+template <typename R>
+struct IfaceZ {
+  R ar[6][Plane<3>::N];      // alpha, ring of planes (m mod 6)
+  R xp[Plane<3>::PY][kZX + 2];   // x-smoothed plane, x halo 1, y halo 3
+  R xy[5][Plane<1>::N];      // x-y-smoothed planes (m mod 5)
+  R s2[3][Plane<1>::N];      // smoothed alpha (m mod 3)
+  R T[4][Plane<1>::N];       // temperature (m mod 4)
+  R c[4][Plane<1>::N];       // concentration (m mod 4), when transported
+  R nx[kZY][kZX + 1];        // face normals of the current plane
+  R ny[kZY + 1][kZX];
+};
+
+// smooth the staged alpha plane m in x and y into xy[m mod 5] (the caller
+// synchronises after staging and after this)
+template <typename R>
+__device__ __forceinline__ void iface_plane_xy(IfaceZ<R>& S, int m, const R* wx, const R* wy) {
+  using P3 = Plane<3>;
+  using P1 = Plane<1>;
+  const R* __restrict__ ar = S.ar[(m % 6 + 6) % 6];
+  for (int ly = threadIdx.y - 3; ly < kZY + 3; ly += kZY)
+    for (int lx = threadIdx.x - 1; lx < kZX + 1; lx += kZX) {
+      const int e = P3::at(lx, ly);
+      S.xp[ly + 3][lx + 1] = wx[0] * ar[e - 2] + wx[1] * ar[e - 1] + wx[2] * ar[e] +
+                             wx[3] * ar[e + 1] + wx[4] * ar[e + 2];
+    }
+  __syncthreads();
+  R* __restrict__ xy = S.xy[(m % 5 + 5) % 5];
+  for (int ly = threadIdx.y - 1; ly < kZY + 1; ly += kZY)
+    for (int lx = threadIdx.x - 1; lx < kZX + 1; lx += kZX)
+      xy[P1::at(lx, ly)] = wy[0] * S.xp[ly + 1][lx + 1] + wy[1] * S.xp[ly + 2][lx + 1] +
+                           wy[2] * S.xp[ly + 3][lx + 1] + wy[3] * S.xp[ly + 4][lx + 1] +
+                           wy[4] * S.xp[ly + 5][lx + 1];
+}
+
+// smoothed plane m from the x-y-smoothed planes m-2 .. m+2
+template <typename R>
+__device__ __forceinline__ void iface_plane_z(IfaceZ<R>& S, int m, const R* wz) {
+  const R* __restrict__ q0 = S.xy[((m - 2) % 5 + 5) % 5];
+  const R* __restrict__ q1 = S.xy[((m - 1) % 5 + 5) % 5];
+  const R* __restrict__ q2 = S.xy[(m % 5 + 5) % 5];
+  const R* __restrict__ q3 = S.xy[((m + 1) % 5 + 5) % 5];
+  const R* __restrict__ q4 = S.xy[((m + 2) % 5 + 5) % 5];
+  R* __restrict__ o = S.s2[(m % 3 + 3) % 3];
+  for (int e = threadIdx.x + kZX * threadIdx.y; e < Plane<1>::N; e += kZT)
+    o[e] = wz[0] * q0[e] + wz[1] * q1[e] + wz[2] * q2[e] + wz[3] * q3[e] + wz[4] * q4[e];
+}
+
+// normal on the low x-face (D = 0) or y-face (D = 1) of local cell (lx, ly)
+// of plane c, with the planes below (m) and above (p): grad / (|grad| + eps_n),
+// the normal derivative across the face and each tangential derivative the
+// mean of the two cells' central differences
 template <int D, typename R>
-__device__ __forceinline__ R face_normal(const R* __restrict__ s2, int lx, int ly, int lz, R ih,
-                                         R epsn) {
-  const int dx = D == 0, dy = D == 1, dz = D == 2;
-  R gd = (s2[Tile<1>::at(lx, ly, lz)] - s2[Tile<1>::at(lx - dx, ly - dy, lz - dz)]) * ih;
-  R sq = gd * gd;
+__device__ __forceinline__ R plane_normal(const R* __restrict__ m, const R* __restrict__ c,
+                                          const R* __restrict__ p, int lx, int ly, R ih, R epsn) {
+  using P1 = Plane<1>;
+  const int e = P1::at(lx, ly);
+  const int sd = D == 0 ? 1 : P1::PX;   // stride along the face normal
+  const int st = D == 0 ? P1::PX : 1;   // stride along the in-plane tangent
   const R q = ih * R(0.25);
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    if (t == D) continue;
-    const int ox = t == 0, oy = t == 1, oz = t == 2;
-    R gt = ((s2[Tile<1>::at(lx + ox, ly + oy, lz + oz)] - s2[Tile<1>::at(lx - ox, ly - oy, lz - oz)]) +
-            (s2[Tile<1>::at(lx - dx + ox, ly - dy + oy, lz - dz + oz)] -
-             s2[Tile<1>::at(lx - dx - ox, ly - dy - oy, lz - dz - oz)])) * q;
-    sq += gt * gt;
-  }
+  const R gd = (c[e] - c[e - sd]) * ih;
+  const R gt = ((c[e + st] - c[e - st]) + (c[e - sd + st] - c[e - sd - st])) * q;
+  const R gz = ((p[e] - m[e]) + (p[e - sd] - m[e - sd])) * q;
+  // tangential terms in axis order, as for the z-face
+  const R sq = gd * gd + gt * gt + gz * gz;
   return gd / (sqrt(sq) + epsn);
 }
 
+// normal on the face between plane c (below) and plane p (above)
 template <typename R>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
+__device__ __forceinline__ R z_normal(const R* __restrict__ c, const R* __restrict__ p, int lx,
+                                      int ly, R ih, R epsn) {
+  using P1 = Plane<1>;
+  const int e = P1::at(lx, ly);
+  const R q = ih * R(0.25);
+  const R gd = (p[e] - c[e]) * ih;
+  const R gx = ((p[e + 1] - p[e - 1]) + (c[e + 1] - c[e - 1])) * q;
+  const R gy = ((p[e + P1::PX] - p[e - P1::PX]) + (c[e + P1::PX] - c[e - P1::PX])) * q;
+  const R sq = gd * gd + gx * gx + gy * gy;
+  return gd / (sqrt(sq) + epsn);
+}
+
+// binomial weights of K passes of [1,2,1]/4 on an axis of n cells (identity
+// on an axis of one cell)
+template <typename R>
+__device__ __forceinline__ void binomial5(int K, int n, R* w) {
+  const bool id = n == 1 || K == 0;
+  w[0] = (!id && K == 2) ? R(0.0625) : R(0);
+  w[1] = id ? R(0) : (K == 2 ? R(0.25) : R(0.25));
+  w[2] = id ? R(1) : (K == 2 ? R(0.375) : R(0.5));
+  w[3] = w[1];
+  w[4] = w[0];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kZT, sizeof(R) == 4 ? 4 : 2)
     k_interface(Geo g, PhysR<R> ph, TBC tb, int passes, const R* __restrict__ alpha,
                 const R* __restrict__ T, const R* __restrict__ conc, R* __restrict__ kappa,
                 R* __restrict__ M0, R* __restrict__ M1, R* __restrict__ M2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  IfaceShared<R>& S = *reinterpret_cast<IfaceShared<R>*>(smem_raw);
-  stage<3, F_EVEN, 0>(S.a, alpha, g, tb);
-  stage<1, F_TEMP, 0>(S.T, T, g, tb);
-  if (conc) stage<1, F_EVEN, 0>(S.c, conc, g, tb);
-  __syncthreads();
-  if (passes >= 1) {
-    smooth_pass<3, 2>(g, S.a, S.s1);
-    __syncthreads();
-    if (passes >= 2) smooth_pass<2, 1>(g, S.s1, S.s2);
-    else copy_tile<2, 1>(S.s1, S.s2);
-  } else {
-    copy_tile<3, 1>(S.a, S.s2);
-  }
-  __syncthreads();
-  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
+  IfaceZ<R>& S = *reinterpret_cast<IfaceZ<R>*>(smem_raw);
+  using P1 = Plane<1>;
+  using P3 = Plane<3>;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const R ih = ph.ih;
-  const R epsn = ph.eps_n;
-  if (i <= nx && j < ny && k < nz) {
-    S.nx[tz][ty][tx] = face_normal<0>(S.s2, tx, ty, tz, ih, epsn);
-    if (tx == kBX - 1 && i + 1 <= nx) S.nx[tz][ty][tx + 1] = face_normal<0>(S.s2, tx + 1, ty, tz, ih, epsn);
-  }
-  if (i < nx && j <= ny && k < nz) {
-    S.ny[tz][ty][tx] = face_normal<1>(S.s2, tx, ty, tz, ih, epsn);
-    if (ty == kBY - 1 && j + 1 <= ny) S.ny[tz][ty + 1][tx] = face_normal<1>(S.s2, tx, ty + 1, tz, ih, epsn);
-  }
-  if (i < nx && j < ny && k <= nz) {
-    S.nz[tz][ty][tx] = face_normal<2>(S.s2, tx, ty, tz, ih, epsn);
-    if (tz == kBZ - 1 && k + 1 <= nz) S.nz[tz + 1][ty][tx] = face_normal<2>(S.s2, tx, ty, tz + 1, ih, epsn);
-  }
-  __syncthreads();
-  if (i >= nx || j >= ny || k >= nz) return;
-  const int c = (k * ny + j) * nx + i;
-  R kap = 0;
-  kap += (S.nx[tz][ty][tx + 1] - S.nx[tz][ty][tx]) * ih;
-  kap += (S.ny[tz][ty + 1][tx] - S.ny[tz][ty][tx]) * ih;
-  kap += (S.nz[tz + 1][ty][tx] - S.nz[tz][ty][tx]) * ih;
-  kappa[c] = kap;
-  // Marangoni vector from central differences of alpha, smoothed alpha, sigma(T)
-  const R i2h = R(0.5) * ih;
-  R gv[3], tv[3], sv[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int ox = d == 0, oy = d == 1, oz = d == 2;
-    gv[d] = (S.a[Tile<3>::at(tx + ox, ty + oy, tz + oz)] - S.a[Tile<3>::at(tx - ox, ty - oy, tz - oz)]) * i2h;
-    tv[d] = (S.s2[Tile<1>::at(tx + ox, ty + oy, tz + oz)] - S.s2[Tile<1>::at(tx - ox, ty - oy, tz - oz)]) * i2h;
-    const R Tp = S.T[Tile<1>::at(tx + ox, ty + oy, tz + oz)];
-    const R Tm = S.T[Tile<1>::at(tx - ox, ty - oy, tz - oz)];
-    // central difference of the sigma field (Eq. 5 as a cell field).  In
-    // float it is taken as dsigma/dT (T+ - T-), the same number for the
-    // linear sigma(T): the difference of two neighbouring temperatures is
-    // exact, while sigma0 + dsigma/dT (T - T0) rounded to float at
-    // sigma ~ 1.9 keeps only ~4 digits of a variation of ~1e-3
-    if (conc) {
-      // sigma(c, T) of Eq. 5: in float the exact neighbour differences
-      // again, in double the difference of the two cells' sigma values
-      const R cp = S.c[Tile<1>::at(tx + ox, ty + oy, tz + oz)];
-      const R cm = S.c[Tile<1>::at(tx - ox, ty - oy, tz - oz)];
-      if (sizeof(R) == 4) sv[d] = (ph.dsdT * (Tp - Tm) + ph.dsdc * (cp - cm)) * i2h;
-      else sv[d] = (sigma_rc(Tp, cp, ph) - sigma_rc(Tm, cm, ph)) * i2h;
-    } else if (sizeof(R) == 4) {
-      sv[d] = ph.dsdT * (Tp - Tm) * i2h;
-    } else {
-      sv[d] = (sigma_r(Tp, ph) - sigma_r(Tm, ph)) * i2h;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * kZX + tx, j = blockIdx.y * kZY + ty;
+  const int z0 = blockIdx.z * kZKI;
+  const int z1 = min(z0 + kZKI, nz);
+  const bool in = zcols_interior(g, 3);
+  const bool col = i < nx && j < ny;
+  const R ih = ph.ih, i2h = R(0.5) * ph.ih, epsn = ph.eps_n;
+  const int K = passes < 2 ? passes : 2;
+  R wx[5], wy[5], wz[5];
+  binomial5(K, nx, wx);
+  binomial5(K, ny, wy);
+  binomial5(K, nz, wz);
+  // warm-up: alpha planes z0-3 .. z0+2 smoothed in x and y, smoothed planes
+  // z0-1 and z0, temperature (and concentration) planes z0-1 and z0
+  for (int m = z0 - 3; m <= z0 + 2; ++m) {
+    if (m == z0 - 1 || m == z0) {
+      stage_plane<1, F_TEMP>(S.T[(m % 4 + 4) % 4], T, g, tb, in, m);
+      if (conc) stage_plane<1, F_EVEN>(S.c[(m % 4 + 4) % 4], conc, g, tb, in, m);
+    }
+    stage_plane<3, F_EVEN>(S.ar[(m % 6 + 6) % 6], alpha, g, tb, in, m);
+    __syncthreads();
+    iface_plane_xy(S, m, wx, wy);
+    __syncthreads();
+    if (m == z0 + 1 || m == z0 + 2) {
+      iface_plane_z(S, m - 2, wz);
+      __syncthreads();
     }
   }
-  R gn = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
-  R tn = sqrt(tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]) + epsn;
-  R n0 = tv[0] / tn, n1 = tv[1] / tn, n2 = tv[2] / tn;
-  R ns = n0 * sv[0] + n1 * sv[1] + n2 * sv[2];
-  M0[c] = gn * (sv[0] - n0 * ns);
-  M1[c] = gn * (sv[1] - n1 * ns);
-  M2[c] = gn * (sv[2] - n2 * ns);
+  R nzl = R(0);   // normal on the low z-face of the current plane
+  if (col) nzl = z_normal(S.s2[((z0 - 1) % 3 + 3) % 3], S.s2[z0 % 3], tx, ty, ih, epsn);
+  // the planes a step needs first are copied one step ahead
+  plane_async<3, F_EVEN>(S.ar[(z0 + 3) % 6], alpha, g, tb, in, z0 + 3);
+  plane_async<1, F_TEMP>(S.T[(z0 + 1) % 4], T, g, tb, in, z0 + 1);
+  if (conc) plane_async<1, F_EVEN>(S.c[(z0 + 1) % 4], conc, g, tb, in, z0 + 1);
+  cp_async_commit();
+  for (int k = z0; k < z1; ++k) {
+    cp_async_wait_all();
+    __syncthreads();
+    // the slots of alpha k - 2 and T k - 2, last read by the previous step
+    if (k + 1 < z1) {
+      plane_async<3, F_EVEN>(S.ar[(k + 4) % 6], alpha, g, tb, in, k + 4);
+      plane_async<1, F_TEMP>(S.T[(k + 2) % 4], T, g, tb, in, k + 2);
+      if (conc) plane_async<1, F_EVEN>(S.c[(k + 2) % 4], conc, g, tb, in, k + 2);
+      cp_async_commit();
+    }
+    iface_plane_xy(S, k + 3, wx, wy);
+    __syncthreads();
+    iface_plane_z(S, k + 1, wz);
+    __syncthreads();
+    const R* __restrict__ sm = S.s2[((k - 1) % 3 + 3) % 3];
+    const R* __restrict__ sc = S.s2[k % 3];
+    const R* __restrict__ sp = S.s2[(k + 1) % 3];
+    if (i <= nx && j < ny) S.nx[ty][tx] = plane_normal<0>(sm, sc, sp, tx, ty, ih, epsn);
+    if (i < nx && j <= ny) S.ny[ty][tx] = plane_normal<1>(sm, sc, sp, tx, ty, ih, epsn);
+    if (ty == 0) {
+      if (i < nx && blockIdx.y * kZY + kZY <= ny)
+        S.ny[kZY][tx] = plane_normal<1>(sm, sc, sp, tx, kZY, ih, epsn);
+    } else if (ty == 1 && tx < kZY) {
+      if (blockIdx.x * kZX + kZX <= nx && blockIdx.y * kZY + tx < ny)
+        S.nx[tx][kZX] = plane_normal<0>(sm, sc, sp, kZX, tx, ih, epsn);
+    }
+    R nzh = R(0);
+    if (col) nzh = z_normal(sc, sp, tx, ty, ih, epsn);
+    __syncthreads();
+    if (col) {
+      const int c = (k * ny + j) * nx + i;
+      R kap = 0;
+      kap += (S.nx[ty][tx + 1] - S.nx[ty][tx]) * ih;
+      kap += (S.ny[ty + 1][tx] - S.ny[ty][tx]) * ih;
+      kap += (nzh - nzl) * ih;
+      kappa[c] = kap;
+      // Marangoni vector from central differences of alpha, smoothed alpha, sigma(T)
+      const R* __restrict__ am = S.ar[((k - 1) % 6 + 6) % 6];
+      const R* __restrict__ ac = S.ar[k % 6];
+      const R* __restrict__ ap = S.ar[(k + 1) % 6];
+      const R* __restrict__ Tm = S.T[((k - 1) % 4 + 4) % 4];
+      const R* __restrict__ Tc = S.T[k % 4];
+      const R* __restrict__ Tp = S.T[(k + 1) % 4];
+      const int e3 = P3::at(tx, ty), e1 = P1::at(tx, ty);
+      R gv[3], tv[3], sv[3], cP[3], cM[3], TP[3], TM[3];
+      gv[0] = (ac[e3 + 1] - ac[e3 - 1]) * i2h;
+      gv[1] = (ac[e3 + P3::PX] - ac[e3 - P3::PX]) * i2h;
+      gv[2] = (ap[e3] - am[e3]) * i2h;
+      tv[0] = (sc[e1 + 1] - sc[e1 - 1]) * i2h;
+      tv[1] = (sc[e1 + P1::PX] - sc[e1 - P1::PX]) * i2h;
+      tv[2] = (sp[e1] - sm[e1]) * i2h;
+      TP[0] = Tc[e1 + 1];      TM[0] = Tc[e1 - 1];
+      TP[1] = Tc[e1 + P1::PX]; TM[1] = Tc[e1 - P1::PX];
+      TP[2] = Tp[e1];          TM[2] = Tm[e1];
+      if (conc) {
+        const R* __restrict__ cm_ = S.c[((k - 1) % 4 + 4) % 4];
+        const R* __restrict__ cc_ = S.c[k % 4];
+        const R* __restrict__ cp_ = S.c[(k + 1) % 4];
+        cP[0] = cc_[e1 + 1];      cM[0] = cc_[e1 - 1];
+        cP[1] = cc_[e1 + P1::PX]; cM[1] = cc_[e1 - P1::PX];
+        cP[2] = cp_[e1];          cM[2] = cm_[e1];
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        // central difference of the sigma field (Eq. 5 as a cell field).  In
+        // float it is taken as dsigma/dT (T+ - T-), the same number for the
+        // linear sigma(T): the difference of two neighbouring temperatures is
+        // exact, while sigma0 + dsigma/dT (T - T0) rounded to float at
+        // sigma ~ 1.9 keeps only ~4 digits of a variation of ~1e-3
+        if (conc) {
+          // sigma(c, T) of Eq. 5: in float the exact neighbour differences
+          // again, in double the difference of the two cells' sigma values
+          if (sizeof(R) == 4) sv[d] = (ph.dsdT * (TP[d] - TM[d]) + ph.dsdc * (cP[d] - cM[d])) * i2h;
+          else sv[d] = (sigma_rc(TP[d], cP[d], ph) - sigma_rc(TM[d], cM[d], ph)) * i2h;
+        } else if (sizeof(R) == 4) {
+          sv[d] = ph.dsdT * (TP[d] - TM[d]) * i2h;
+        } else {
+          sv[d] = (sigma_r(TP[d], ph) - sigma_r(TM[d], ph)) * i2h;
+        }
+      }
+      R gn = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+      R tn = sqrt(tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]) + epsn;
+      R n0 = tv[0] / tn, n1 = tv[1] / tn, n2 = tv[2] / tn;
+      R ns = n0 * sv[0] + n1 * sv[1] + n2 * sv[2];
+      M0[c] = gn * (sv[0] - n0 * ns);
+      M1[c] = gn * (sv[1] - n1 * ns);
+      M2[c] = gn * (sv[2] - n2 * ns);
+    }
+    nzl = nzh;
+  }
 }
 
 template <typename R>
 void launch_interface(const Geo& g, const Phys& ph, const TBC& tb, int passes, const R* alpha,
                       const R* T, const R* c, R* kappa, R* M0, R* M1, R* M2, cudaStream_t s) {
-  const int smem = (int)sizeof(IfaceShared<R>);
+  const int smem = (int)sizeof(IfaceZ<R>);
   cudaFuncSetAttribute(k_interface<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_interface<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       cudaSharedmemCarveoutMaxShared);
-  k_interface<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
+  k_interface<R><<<zmarch_grid(g, kZKI), dim3(kZX, kZY), smem, s>>>(
       g, make_physr<R>(ph, g), tb, passes, alpha, T, c, kappa, M0, M1, M2);
 }
 
 // ---------------------------------------------------------------------------
-// scalar transport (alpha, T) and stage update
-
-// face fluxes of one tile: [0] alpha advection, [1] T advection, [2] T conduction
-template <typename R>
-struct ScalFlux {
-  R x[3][kBZ][kBY][kBX + 1];
-  R y[3][kBZ][kBY + 1][kBX];
-  R z[3][kBZ + 1][kBY][kBX];
-};
-
-template <typename R>
-struct ScalShared {
-  R a[Tile<3>::N];
-  R T[Tile<3>::N];
-  ScalFlux<R> F;
-};
-
-// advective fluxes of alpha and T and the conductive flux of T through the
-// low D-face of local cell (lx,ly,lz)
 // limiter ratios of the bounded phase-fraction option (null: plain WENO5)
 template <typename R>
 struct FctRatios {
@@ -421,97 +601,197 @@ __device__ __forceinline__ R fct_flux(const FctRatios<R>& f, const Geo& g, bool 
   return FL + th * A;
 }
 
+// scalar transport (alpha, T) and stage update
+//
+// Plane k of alpha and T is staged with an x-y halo of 3 (the WENO5 reach);
+// the z-direction stencil lives in each thread's registers (a window of its
+// column from k-3 to k+3), and the flux through the face between planes k
+// and k+1 is evaluated once and carried to the next plane.  Every x- and
+// y-face flux is evaluated once per plane: each thread takes the low face of
+// its cell, one warp the high y-faces of the tile's last row, another the
+// high x-faces of its last column.
+constexpr int kZKS = 16;   // planes per CTA
+
+// one cell of column (i, j) at height k (any k: ghost planes go through the
+// boundary rules)
+template <int KIND, typename R>
+__device__ __forceinline__ R col_ld(const R* __restrict__ a, const Geo& g, const TBC& tb, int i,
+                                    int j, int k) {
+  if (k >= 0 && k < g.n[2]) return __ldg(a + ((k * g.n[1] + j) * g.n[0] + i));
+  return KIND == F_EVEN ? ld_even(a, g, i, j, k) : ld_T(a, g, tb, i, j, k);
+}
+
+// velocity on the low D-face of cell (i, j, k): direct for a face strictly
+// inside the domain along D, through the boundary rules otherwise
 template <int D, typename R>
-__device__ __forceinline__ void scalar_face(const ScalShared<R>& S, const PhysR<R>& ph, const R Uf,
-                                            int lx, int ly, int lz, R& Fa, R& FT, R& Df,
-                                            const FctRatios<R>& fct, const Geo& g, bool in,
-                                            int gi, int gj, int gk) {
-  const int dx = D == 0, dy = D == 1, dz = D == 2;
-  R av[6], tv[6];
-#pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    const int o = m - 3;
-    av[m] = S.a[Tile<3>::at(lx + o * dx, ly + o * dy, lz + o * dz)];
-    tv[m] = S.T[Tile<3>::at(lx + o * dx, ly + o * dy, lz + o * dz)];
-  }
-  Fa = upwind_flux(Uf, av, ph.eps_a);
-  if (fct.Rp) Fa = fct_flux<D>(fct, g, in, gi, gj, gk, Uf, av[2], av[3], Fa);
-  FT = upwind_flux(Uf, tv, ph.eps_T);
-  R lL = mixr(av[2], ph.lam), lR = mixr(av[3], ph.lam);
-  R lf = R(2) * lL * lR / (lL + lR);
+__device__ __forceinline__ R face_u(const R* __restrict__ u, const Geo& g, bool in, int i, int j,
+                                    int k) {
+  const int f = D == 0 ? i : (D == 1 ? j : k);
+  if (in || (f >= 1 && f <= g.n[D] - 1)) return __ldg(u + ((k * g.n[1] + j) * g.n[0] + i));
+  return ld_vel<D>(u, g, i, j, k);
+}
+
+// advective fluxes of alpha and T and the conductive flux of T through one
+// face from the six values of each field around it (av[2] left, av[3] right)
+template <typename R>
+__device__ __forceinline__ void scal_flux(const R* av, const R* tv, R U, const PhysR<R>& ph,
+                                          R& Fa, R& FT, R& Df) {
+  Fa = upwind_flux(U, av, ph.eps_a);
+  FT = upwind_flux(U, tv, ph.eps_T);
+  const R lL = mixr(av[2], ph.lam), lR = mixr(av[3], ph.lam);
+  const R lf = R(2) * lL * lR / (lL + lR);
   Df = lf * (tv[3] - tv[2]) * ph.ih;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 4 : 1)
+struct ScalZ {
+  R a[2][Plane<3>::N];   // alpha, planes k and k + 1 (k mod 2)
+  R T[2][Plane<3>::N];
+  R fx[3][kZY][kZX + 1];   // [0] alpha advection, [1] T advection, [2] T conduction
+  R fy[3][kZY + 1][kZX];
+};
+
+// x- or y-face (D = 0, 1) fluxes of the staged plane through the low face of
+// local cell (lx, ly), global cell (i, j, k)
+template <int D, typename R>
+__device__ __forceinline__ void plane_face(const R* __restrict__ sa, const R* __restrict__ sT,
+                                           const PhysR<R>& ph, const Geo& g,
+                                           const Fields<R>& X, const FctRatios<R>& fct, bool in,
+                                           int lx, int ly, int i, int j, int k, R& Fa, R& FT,
+                                           R& Df) {
+  using P = Plane<3>;
+  R av[6], tv[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const int e = D == 0 ? P::at(lx + m - 3, ly) : P::at(lx, ly + m - 3);
+    av[m] = sa[e];
+    tv[m] = sT[e];
+  }
+  const R U = face_u<D>(X.u[D], g, in, i, j, k);
+  scal_flux(av, tv, U, ph, Fa, FT, Df);
+  if (fct.Rp) Fa = fct_flux<D>(fct, g, in, i, j, k, U, av[2], av[3], Fa);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kZT, sizeof(R) == 4 ? 4 : 2)
     k_scalars(Geo g, PhysR<R> ph, TBC tb, Fields<R> X, Fields<R> Sn, Fields<R> Y,
               const double* __restrict__ dtp, R a, R b, R xc, R yc, R qamp, R ir2,
               FctRatios<R> fct) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ScalShared<R>& S = *reinterpret_cast<ScalShared<R>*>(smem_raw);
-  stage<3, F_EVEN, 0>(S.a, X.alpha, g, tb);
-  stage<3, F_TEMP, 0>(S.T, X.T, g, tb);
-  const bool in = tile_interior(g, 3);
-  __syncthreads();
-  const R dt = (R)dtp[0];
-  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
+  __shared__ ScalZ<R> S;
+  using P = Plane<3>;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const R ih = ph.ih;
-  ScalFlux<R>& F = S.F;
-  if (i <= nx && j < ny && k < nz) {
-    scalar_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i, j, k), tx, ty, tz, F.x[0][tz][ty][tx], F.x[1][tz][ty][tx], F.x[2][tz][ty][tx],
-                   fct, g, in, i, j, k);
-    if (tx == kBX - 1 && i + 1 <= nx)
-      scalar_face<0>(S, ph, g_vel<0>(X.u[0], g, in, i + 1, j, k), tx + 1, ty, tz, F.x[0][tz][ty][tx + 1], F.x[1][tz][ty][tx + 1],
-                     F.x[2][tz][ty][tx + 1], fct, g, in, i + 1, j, k);
-  }
-  if (i < nx && j <= ny && k < nz) {
-    scalar_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j, k), tx, ty, tz, F.y[0][tz][ty][tx], F.y[1][tz][ty][tx], F.y[2][tz][ty][tx],
-                   fct, g, in, i, j, k);
-    if (ty == kBY - 1 && j + 1 <= ny)
-      scalar_face<1>(S, ph, g_vel<1>(X.u[1], g, in, i, j + 1, k), tx, ty + 1, tz, F.y[0][tz][ty + 1][tx], F.y[1][tz][ty + 1][tx],
-                     F.y[2][tz][ty + 1][tx], fct, g, in, i, j + 1, k);
-  }
-  if (i < nx && j < ny && k <= nz) {
-    scalar_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k), tx, ty, tz, F.z[0][tz][ty][tx], F.z[1][tz][ty][tx], F.z[2][tz][ty][tx],
-                   fct, g, in, i, j, k);
-    if (tz == kBZ - 1 && k + 1 <= nz)
-      scalar_face<2>(S, ph, g_vel<2>(X.u[2], g, in, i, j, k + 1), tx, ty, tz + 1, F.z[0][tz + 1][ty][tx], F.z[1][tz + 1][ty][tx],
-                     F.z[2][tz + 1][ty][tx], fct, g, in, i, j, k + 1);
-  }
-  __syncthreads();
-  if (i >= nx || j >= ny || k >= nz) return;
-  const int c = (k * ny + j) * nx + i;
-  R Ra = 0, RT = 0, Dif = 0;
-  Ra -= (F.x[0][tz][ty][tx + 1] - F.x[0][tz][ty][tx]) * ih;
-  RT -= (F.x[1][tz][ty][tx + 1] - F.x[1][tz][ty][tx]) * ih;
-  Dif += (F.x[2][tz][ty][tx + 1] - F.x[2][tz][ty][tx]) * ih;
-  Ra -= (F.y[0][tz][ty + 1][tx] - F.y[0][tz][ty][tx]) * ih;
-  RT -= (F.y[1][tz][ty + 1][tx] - F.y[1][tz][ty][tx]) * ih;
-  Dif += (F.y[2][tz][ty + 1][tx] - F.y[2][tz][ty][tx]) * ih;
-  Ra -= (F.z[0][tz + 1][ty][tx] - F.z[0][tz][ty][tx]) * ih;
-  RT -= (F.z[1][tz + 1][ty][tx] - F.z[1][tz][ty][tx]) * ih;
-  Dif += (F.z[2][tz + 1][ty][tx] - F.z[2][tz][ty][tx]) * ih;
-  const R al = S.a[Tile<3>::at(tx, ty, tz)];
-  const R rcp = mixr(al, ph.rcp);
-  RT += Dif / rcp;
-  if (qamp != R(0)) {
-    const R i2h = R(0.5) * ih;
-    R gx = (S.a[Tile<3>::at(tx + 1, ty, tz)] - S.a[Tile<3>::at(tx - 1, ty, tz)]) * i2h;
-    R gy = (S.a[Tile<3>::at(tx, ty + 1, tz)] - S.a[Tile<3>::at(tx, ty - 1, tz)]) * i2h;
-    R gz = (S.a[Tile<3>::at(tx, ty, tz + 1)] - S.a[Tile<3>::at(tx, ty, tz - 1)]) * i2h;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * kZX + tx, j = blockIdx.y * kZY + ty;
+  const int z0 = blockIdx.z * kZKS;
+  const int z1 = min(z0 + kZKS, nz);
+  const bool in = zcols_interior(g, 3);
+  const bool col = i < nx && j < ny;
+  const R dt = (R)dtp[0];
+  const R ih = ph.ih, i2h = R(0.5) * ph.ih;
+  // the Gaussian surface flux depends on (i, j) only
+  R qcol = R(0);
+  if (qamp != R(0) && col) {
     R dx = (R(i) + R(0.5)) * ph.h - xc, dy = (R(j) + R(0.5)) * ph.h - yc;
     if (g.bc[0] == PER) dx = dx - ph.L[0] * floor(dx / ph.L[0] + R(0.5));
     if (g.bc[1] == PER) dy = dy - ph.L[1] * floor(dy / ph.L[1] + R(0.5));
-    R q = qamp * exp(R(-2) * (dx * dx + dy * dy) * ir2);
-    R gn = sqrt(gx * gx + gy * gy + gz * gz);
-    RT += q * gn / rcp;
+    qcol = qamp * exp(R(-2) * (dx * dx + dy * dy) * ir2);
   }
-  R Ea = al + dt * Ra;
-  R ET = S.T[Tile<3>::at(tx, ty, tz)] + dt * RT;
-  Y.alpha[c] = a * Sn.alpha[c] + b * Ea;
-  Y.T[c] = a * Sn.T[c] + b * ET;
+  // column window: wa[m], wt[m] = alpha, T at height k - 3 + m
+  R wa[7], wt[7];
+  R fz0[3] = {R(0), R(0), R(0)};   // fluxes through the low z-face of plane k
+  if (col) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      wa[m] = col_ld<F_EVEN>(X.alpha, g, tb, i, j, z0 - 3 + m);
+      wt[m] = col_ld<F_TEMP>(X.T, g, tb, i, j, z0 - 3 + m);
+    }
+    const R U = face_u<2>(X.u[2], g, false, i, j, z0);
+    scal_flux(wa, wt, U, ph, fz0[0], fz0[1], fz0[2]);
+    if (fct.Rp) fz0[0] = fct_flux<2>(fct, g, z0 >= 1, i, j, z0, U, wa[2], wa[3], fz0[0]);
+  }
+  // the next plane and the next column values, loaded one step ahead
+  plane_async<3, F_EVEN>(S.a[z0 & 1], X.alpha, g, tb, in, z0);
+  plane_async<3, F_TEMP>(S.T[z0 & 1], X.T, g, tb, in, z0);
+  cp_async_commit();
+  R na = R(0), nt = R(0);
+  for (int k = z0; k < z1; ++k) {
+    cp_async_wait_all();
+    __syncthreads();
+    // the other buffer held plane k - 1, last read before the previous step's
+    // second barrier
+    if (k + 1 < z1) {
+      plane_async<3, F_EVEN>(S.a[(k + 1) & 1], X.alpha, g, tb, in, k + 1);
+      plane_async<3, F_TEMP>(S.T[(k + 1) & 1], X.T, g, tb, in, k + 1);
+      cp_async_commit();
+      if (col) {
+        na = col_ld<F_EVEN>(X.alpha, g, tb, i, j, k + 4);
+        nt = col_ld<F_TEMP>(X.T, g, tb, i, j, k + 4);
+      }
+    }
+    const R* __restrict__ sa = S.a[k & 1];
+    const R* __restrict__ sT = S.T[k & 1];
+    if (i <= nx && j < ny)
+      plane_face<0>(sa, sT, ph, g, X, fct, in, tx, ty, i, j, k, S.fx[0][ty][tx], S.fx[1][ty][tx],
+                    S.fx[2][ty][tx]);
+    if (i < nx && j <= ny)
+      plane_face<1>(sa, sT, ph, g, X, fct, in, tx, ty, i, j, k, S.fy[0][ty][tx], S.fy[1][ty][tx],
+                    S.fy[2][ty][tx]);
+    if (ty == 0) {
+      // high y-faces of the tile's last row
+      const int jj = blockIdx.y * kZY + kZY;
+      if (i < nx && jj <= ny)
+        plane_face<1>(sa, sT, ph, g, X, fct, in, tx, kZY, i, jj, k, S.fy[0][kZY][tx], S.fy[1][kZY][tx],
+                      S.fy[2][kZY][tx]);
+    } else if (ty == 1 && tx < kZY) {
+      // high x-faces of the tile's last column, one row per lane
+      const int ii = blockIdx.x * kZX + kZX, jj = blockIdx.y * kZY + tx;
+      if (ii <= nx && jj < ny)
+        plane_face<0>(sa, sT, ph, g, X, fct, in, kZX, tx, ii, jj, k, S.fx[0][tx][kZX],
+                      S.fx[1][tx][kZX], S.fx[2][tx][kZX]);
+    }
+    R fz1[3] = {R(0), R(0), R(0)};   // fluxes through the face between k and k + 1
+    R gx = R(0), gy = R(0);
+    if (col) {
+      const R U = face_u<2>(X.u[2], g, false, i, j, k + 1);
+      scal_flux(wa + 1, wt + 1, U, ph, fz1[0], fz1[1], fz1[2]);
+      if (fct.Rp) fz1[0] = fct_flux<2>(fct, g, k + 1 <= nz - 1, i, j, k + 1, U, wa[3], wa[4], fz1[0]);
+      if (qamp != R(0)) {
+        gx = (sa[P::at(tx + 1, ty)] - sa[P::at(tx - 1, ty)]) * i2h;
+        gy = (sa[P::at(tx, ty + 1)] - sa[P::at(tx, ty - 1)]) * i2h;
+      }
+    }
+    __syncthreads();
+    if (col) {
+      const int c = (k * ny + j) * nx + i;
+      R Ra = -((S.fx[0][ty][tx + 1] - S.fx[0][ty][tx]) * ih +
+               (S.fy[0][ty + 1][tx] - S.fy[0][ty][tx]) * ih + (fz1[0] - fz0[0]) * ih);
+      R RT = -((S.fx[1][ty][tx + 1] - S.fx[1][ty][tx]) * ih +
+               (S.fy[1][ty + 1][tx] - S.fy[1][ty][tx]) * ih + (fz1[1] - fz0[1]) * ih);
+      const R Dif = (S.fx[2][ty][tx + 1] - S.fx[2][ty][tx]) * ih +
+                    (S.fy[2][ty + 1][tx] - S.fy[2][ty][tx]) * ih + (fz1[2] - fz0[2]) * ih;
+      const R al = wa[3];
+      const R rcp = mixr(al, ph.rcp);
+      RT += Dif / rcp;
+      if (qamp != R(0)) {
+        const R gz = (wa[4] - wa[2]) * i2h;
+        const R gn = sqrt(gx * gx + gy * gy + gz * gz);
+        RT += qcol * gn / rcp;
+      }
+      const R Ea = al + dt * Ra;
+      const R ET = wt[3] + dt * RT;
+      Y.alpha[c] = a * Sn.alpha[c] + b * Ea;
+      Y.T[c] = a * Sn.T[c] + b * ET;
+    }
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      wa[m] = wa[m + 1];
+      wt[m] = wt[m + 1];
+    }
+    wa[6] = na;
+    wt[6] = nt;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) fz0[q] = fz1[q];
+  }
 }
 
 template <typename R>
@@ -522,11 +802,7 @@ void launch_scalars(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, Fi
   double r2 = ph.q_radius * ph.q_radius;
   double qamp = ph.q_power != 0.0 ? 2.0 * ph.q_power / (M_PI * r2) : 0.0;
   double ir2 = ph.q_power != 0.0 ? 1.0 / r2 : 0.0;
-  const int smem = (int)sizeof(ScalShared<R>);
-  cudaFuncSetAttribute(k_scalars<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaFuncSetAttribute(k_scalars<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       cudaSharedmemCarveoutMaxShared);
-  k_scalars<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
+  k_scalars<R><<<zmarch_grid(g, kZKS), dim3(kZX, kZY), 0, s>>>(
       g, make_physr<R>(ph, g), tb, X, Sn, Y, dt, (R)a, (R)b, (R)xc, (R)ph.q_y0, (R)qamp, (R)ir2,
       FctRatios<R>{fct_p, fct_m});
 }
@@ -686,205 +962,435 @@ void launch_concentration(const Geo& g, const Phys& ph, Fields<R> X, Fields<R> S
 
 // ---------------------------------------------------------------------------
 // momentum predictor
+//
+// For component D on its MAC faces: conservative WENO5 advection and the
+// variable-viscosity stress through the sides of the face-centred control
+// volume (normal fluxes at the two cell centres along D, tangential fluxes at
+// the four edges), the balanced-force CSF normal force (Eq. 4 normal term),
+// the face-averaged Marangoni force and gravity.  z-marching: per plane k the
+// velocity planes are staged with an x-y halo of 3 (u and v at k - 1 and k,
+// w at k and k + 1) and alpha with a halo of 1 (k - 1 .. k + 1), with the cell
+// viscosity mu(alpha) formed once per staged plane; the z-direction stencils
+// of u, v and w are register windows of the thread's column, and the fluxes
+// through the z-facing sides of a control volume are carried from one plane
+// to the next.  Every flux is evaluated once: each thread takes those of its
+// own faces, four warps the ones on the tile's high (or low) side.
+constexpr int kZKM = 16;   // planes per CTA
 
-// flux arrays for one component: [0] centre, [1] edge along t1, [2] edge along
-// t2; advective (a) and viscous (v) parts.  Extents kBZ+1 x kBY+1 x kBX+1
-// cover the one extra layer on any axis.
 template <typename R>
-struct MomFlux {
-  R a[3][kBZ + 1][kBY + 1][kBX + 1];
-  R v[3][kBZ + 1][kBY + 1][kBX + 1];
+struct MomZ {
+  R u[3][Plane<3>::N];    // u planes (m mod 3)
+  R v[3][Plane<3>::N];    // v planes (m mod 3)
+  R w[3][Plane<3>::N];    // w planes (m mod 3)
+  R al[4][Plane<1>::N];   // alpha (m mod 4)
+  R mu[3][Plane<1>::N];   // mu(alpha) (m mod 3)
+  // fluxes of the current plane, [0] advective, [1] viscous
+  R c0[2][kZY][kZX + 1];    // u: centre fluxes of cells x0-1 .. x0+31
+  R e0y[2][kZY + 1][kZX];   // u: low y-edges of the faces, rows y0 .. y0+8
+  R c1[2][kZY + 1][kZX];    // v: centre fluxes of cells y0-1 .. y0+7
+  R e1x[2][kZY][kZX + 1];   // v: low x-edges of the faces, columns x0 .. x0+32
+  R e2x[2][kZY][kZX + 1];   // w: low x-edges
+  R e2y[2][kZY + 1][kZX];   // w: low y-edges
 };
 
-template <typename R>
-struct MomShared {
-  R u[3][Tile<3>::N];     // velocity components
-  R mu[Tile<1>::N];       // cell viscosity mu(alpha)
-  MomFlux<R> F;
-};
+__device__ __forceinline__ int mod3(int m) { return (m % 3 + 3) % 3; }
+__device__ __forceinline__ int mod4(int m) { return m & 3; }
 
-template <int D>
-struct Tang {
-  static constexpr int t1 = D == 0 ? 1 : 0;
-  static constexpr int t2 = D == 2 ? 1 : 2;
-};
-
-template <int A>
-__device__ __forceinline__ void sh1(int& x, int& y, int& z, int s) {
-  if (A == 0) x += s;
-  if (A == 1) y += s;
-  if (A == 2) z += s;
+// a velocity component at face (i, j, k) of the thread's own column: direct
+// inside the domain away from the faces the boundary rule fixes
+template <int C, typename R>
+__device__ __forceinline__ R col_vel(const R* __restrict__ a, const Geo& g, int i, int j, int k) {
+  if (point_direct<F_VEL, C>(g, i, j, k)) return __ldg(a + ((k * g.n[1] + j) * g.n[0] + i));
+  return ld_vel<C>(a, g, i, j, k);
 }
 
-// normal momentum fluxes of component D at the centre of local cell
-// (lx,ly,lz): advective U_c WENO5(u_D) with U_c the mean of the two D-faces,
-// viscous normal stress 2 mu du_D/dx_D
-template <int D, typename R>
-__device__ __forceinline__ void centre_flux(const MomShared<R>& S, const PhysR<R>& ph, int lx,
-                                            int ly, int lz, R& Fa, R& Fv) {
+// a cell value at (i, j, k), any index within the stencil reach
+template <int KIND, typename R>
+__device__ __forceinline__ R cell_at(const R* __restrict__ a, const Geo& g, const TBC& tb, int i,
+                                     int j, int k) {
+  if (point_direct<KIND, 0>(g, i, j, k)) return __ldg(a + ((k * g.n[1] + j) * g.n[0] + i));
+  return ld_rule<KIND, 0>(a, g, tb, i, j, k);
+}
+
+// normal flux of a component at the centre of local cell (lx, ly) along the
+// in-plane axis A: WENO5 of the six faces around it with the mean of the
+// cell's two faces as the advecting velocity; viscous 2 mu du/dx_A
+template <int A, typename R>
+__device__ __forceinline__ void mz_centre(const R* __restrict__ q, const R* __restrict__ mu,
+                                          const PhysR<R>& ph, int lx, int ly, R& Fa, R& Fv) {
+  using P3 = Plane<3>;
   R v[6];
 #pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    int x = lx, y = ly, z = lz;
-    sh1<D>(x, y, z, m - 2);
-    v[m] = S.u[D][Tile<3>::at(x, y, z)];
-  }
+  for (int m = 0; m < 6; ++m) v[m] = q[A == 0 ? P3::at(lx + m - 2, ly) : P3::at(lx, ly + m - 2)];
   const R Uc = R(0.5) * (v[2] + v[3]);
   Fa = upwind_flux(Uc, v, ph.eps_u);
-  Fv = R(2) * S.mu[Tile<1>::at(lx, ly, lz)] * (v[3] - v[2]) * ph.ih;
+  Fv = R(2) * mu[Plane<1>::at(lx, ly)] * (v[3] - v[2]) * ph.ih;
 }
 
-// tangential fluxes of component D along T_ at the low T_-edge of the D-face
-// of local cell (lx,ly,lz): advective U_e WENO5(u_D along T_) with U_e the
-// mean of the two T_-faces at the edge, viscous mu_e (du_D/dx_T + du_T/dx_D)
-// with mu_e the mean of the four cells around the edge
-template <int D, int T_, typename R>
-__device__ __forceinline__ void edge_flux(const MomShared<R>& S, const PhysR<R>& ph, int lx,
-                                          int ly, int lz, R& Fa, R& Fv) {
-  R v[6];
-#pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    int x = lx, y = ly, z = lz;
-    sh1<T_>(x, y, z, m - 3);
-    v[m] = S.u[D][Tile<3>::at(x, y, z)];
-  }
-  int x2 = lx, y2 = ly, z2 = lz;   // f - e_D
-  sh1<D>(x2, y2, z2, -1);
-  const R ut_hi = S.u[T_][Tile<3>::at(lx, ly, lz)];
-  const R ut_lo = S.u[T_][Tile<3>::at(x2, y2, z2)];
+// the same along z from the column window v[0..5] (faces k-2 .. k+3 of cell k)
+template <typename R>
+__device__ __forceinline__ void mz_centre_col(const R* v, R mu_c, const PhysR<R>& ph, R& Fa,
+                                              R& Fv) {
+  const R Uc = R(0.5) * (v[2] + v[3]);
+  Fa = upwind_flux(Uc, v, ph.eps_u);
+  Fv = R(2) * mu_c * (v[3] - v[2]) * ph.ih;
+}
+
+// tangential flux at an edge: v[0..5] the advected component at offsets -3..2
+// across the edge (v[2] below, v[3] above), ut_lo / ut_hi the crossing
+// component on the two faces meeting there, mue the mean viscosity of the
+// four cells around the edge
+template <typename R>
+__device__ __forceinline__ void mz_edge(const R* v, R ut_lo, R ut_hi, R mue, const PhysR<R>& ph,
+                                        R& Fa, R& Fv) {
   const R Ue = R(0.5) * (ut_lo + ut_hi);
   Fa = upwind_flux(Ue, v, ph.eps_u);
-  int x3 = lx, y3 = ly, z3 = lz;   // f - e_T
-  sh1<T_>(x3, y3, z3, -1);
-  int x4 = x3, y4 = y3, z4 = z3;   // f - e_T - e_D
-  sh1<D>(x4, y4, z4, -1);
-  const R mue = R(0.25) * (S.mu[Tile<1>::at(lx, ly, lz)] + S.mu[Tile<1>::at(x2, y2, z2)] +
-                           S.mu[Tile<1>::at(x3, y3, z3)] + S.mu[Tile<1>::at(x4, y4, z4)]);
   const R dud_dt = (v[3] - v[2]) * ph.ih;
   const R dut_dd = (ut_hi - ut_lo) * ph.ih;
   Fv = mue * (dud_dt + dut_dd);
 }
 
+template <int T, typename R>
+__device__ __forceinline__ void mz_gather(const R* __restrict__ q, int lx, int ly, R* v) {
+  using P3 = Plane<3>;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) v[m] = q[T == 0 ? P3::at(lx + m - 3, ly) : P3::at(lx, ly + m - 3)];
+}
+
+// u's low y-edge at face (lx, ly) of plane k
+template <typename R>
+__device__ __forceinline__ void mz_e0y(const R* U, const R* V, const R* mu, const PhysR<R>& ph,
+                                       int lx, int ly, R* F) {
+  using P3 = Plane<3>;
+  using P1 = Plane<1>;
+  R v[6];
+  mz_gather<1>(U, lx, ly, v);
+  const R mue = R(0.25) * (mu[P1::at(lx, ly)] + mu[P1::at(lx - 1, ly)] + mu[P1::at(lx, ly - 1)] +
+                           mu[P1::at(lx - 1, ly - 1)]);
+  mz_edge(v, V[P3::at(lx - 1, ly)], V[P3::at(lx, ly)], mue, ph, F[0], F[1]);
+}
+
+// v's low x-edge at face (lx, ly) of plane k
+template <typename R>
+__device__ __forceinline__ void mz_e1x(const R* U, const R* V, const R* mu, const PhysR<R>& ph,
+                                       int lx, int ly, R* F) {
+  using P3 = Plane<3>;
+  using P1 = Plane<1>;
+  R v[6];
+  mz_gather<0>(V, lx, ly, v);
+  const R mue = R(0.25) * (mu[P1::at(lx, ly)] + mu[P1::at(lx, ly - 1)] + mu[P1::at(lx - 1, ly)] +
+                           mu[P1::at(lx - 1, ly - 1)]);
+  mz_edge(v, U[P3::at(lx, ly - 1)], U[P3::at(lx, ly)], mue, ph, F[0], F[1]);
+}
+
+// w's low x-edge (T = 0) or y-edge (T = 1) at z-face (lx, ly) of height k;
+// Qk, Qm: the crossing component (u or v) in planes k and k - 1
+template <int T, typename R>
+__device__ __forceinline__ void mz_e2(const R* W, const R* Qk, const R* Qm, const R* muk,
+                                      const R* mum, const PhysR<R>& ph, int lx, int ly, R* F) {
+  using P3 = Plane<3>;
+  using P1 = Plane<1>;
+  R v[6];
+  mz_gather<T>(W, lx, ly, v);
+  const int e = P1::at(lx, ly), et = T == 0 ? P1::at(lx - 1, ly) : P1::at(lx, ly - 1);
+  const R mue = R(0.25) * (muk[e] + mum[e] + muk[et] + mum[et]);
+  mz_edge(v, Qm[P3::at(lx, ly)], Qk[P3::at(lx, ly)], mue, ph, F[0], F[1]);
+}
+
+// u's (D = 0) or v's (D = 1) z-edge at the face column (lx, ly) between
+// heights kd (below) and ku = kd + 1 (above): v[0..5] the column window at
+// ku-3 .. ku+2, Wu the w plane at ku, muu / mud the viscosity at ku / kd
 template <int D, typename R>
-__device__ __forceinline__ void momentum_component(const Geo& g, const PhysR<R>& ph, const TBC& tb,
-                                                   const Fields<R>& X, const R* __restrict__ kappa,
-                                                   const R* __restrict__ MD, bool in,
-                                                   MomShared<R>& S, R* __restrict__ us, R dt,
-                                                   R* __restrict__ phi) {
-  constexpr int t1 = Tang<D>::t1, t2 = Tang<D>::t2;
-  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-  const int i = blockIdx.x * kBX + tx, j = blockIdx.y * kBY + ty, k = blockIdx.z * kBZ + tz;
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const int gi[3] = {i, j, k};
-  const bool inside = i < nx && j < ny && k < nz;
-  MomFlux<R>& F = S.F;
-  // centre fluxes: cell c at index t_D + 1; the low extra (c - e_D) at index 0
-  if (inside) {
-    int ci = tx, cj = ty, ck = tz;
-    sh1<D>(ci, cj, ck, 1);
-    centre_flux<D>(S, ph, tx, ty, tz, F.a[0][ck][cj][ci], F.v[0][ck][cj][ci]);
-    if (tsel<D>(tx, ty, tz) == 0) {
-      int x = tx, y = ty, z = tz;
-      sh1<D>(x, y, z, -1);
-      centre_flux<D>(S, ph, x, y, z, F.a[0][tz][ty][tx], F.v[0][tz][ty][tx]);
-    }
-  }
-  // edge fluxes along t1 and t2: low edge of face c at index t_T; the high
-  // extra at t_T + 1 (a thread one past the domain on T computes its own low
-  // edge, which is the high edge of the last cell)
-  if (inside || (gi[t1] == g.n[t1] && gi[D] < g.n[D] && gi[t2] < g.n[t2])) {
-    edge_flux<D, t1>(S, ph, tx, ty, tz, F.a[1][tz][ty][tx], F.v[1][tz][ty][tx]);
-    if (inside && tsel<t1>(tx, ty, tz) == tsel<t1>(kBX, kBY, kBZ) - 1) {
-      int x = tx, y = ty, z = tz;
-      sh1<t1>(x, y, z, 1);
-      edge_flux<D, t1>(S, ph, x, y, z, F.a[1][z][y][x], F.v[1][z][y][x]);
-    }
-  }
-  if (inside || (gi[t2] == g.n[t2] && gi[D] < g.n[D] && gi[t1] < g.n[t1])) {
-    edge_flux<D, t2>(S, ph, tx, ty, tz, F.a[2][tz][ty][tx], F.v[2][tz][ty][tx]);
-    if (inside && tsel<t2>(tx, ty, tz) == tsel<t2>(kBX, kBY, kBZ) - 1) {
-      int x = tx, y = ty, z = tz;
-      sh1<t2>(x, y, z, 1);
-      edge_flux<D, t2>(S, ph, x, y, z, F.a[2][z][y][x], F.v[2][z][y][x]);
-    }
-  }
-  __syncthreads();
-  if (inside) {
-    const int c = (k * ny + j) * nx + i;
-    if (g.bc[D] == WALL && gi[D] == 0) {
-      us[c] = R(0);
-      if (phi) phi[c] = R(0);
-    } else {
-      const R ih = ph.ih;
-      int ci = tx, cj = ty, ck = tz;
-      sh1<D>(ci, cj, ck, 1);
-      R A = R(0) - (F.a[0][ck][cj][ci] - F.a[0][tz][ty][tx]) * ih;
-      R V = R(0) + (F.v[0][ck][cj][ci] - F.v[0][tz][ty][tx]) * ih;
-      {
-        int x = tx, y = ty, z = tz;
-        sh1<t1>(x, y, z, 1);
-        A -= (F.a[1][z][y][x] - F.a[1][tz][ty][tx]) * ih;
-        V += (F.v[1][z][y][x] - F.v[1][tz][ty][tx]) * ih;
-      }
-      {
-        int x = tx, y = ty, z = tz;
-        sh1<t2>(x, y, z, 1);
-        A -= (F.a[2][z][y][x] - F.a[2][tz][ty][tx]) * ih;
-        V += (F.v[2][z][y][x] - F.v[2][tz][ty][tx]) * ih;
-      }
-      // forces on the face between cell L = c - e_D and R = c
-      int a = i, b = j, cc = k;
-      sh1<D>(a, b, cc, -1);
-      const R alL = g_even(X.alpha, g, in, a, b, cc), alR = X.alpha[c];
-      const R rho_f = R(0.5) * (mixr(alL, ph.rho) + mixr(alR, ph.rho));
-      const R TL = g_T(X.T, g, tb, in, a, b, cc), TR = X.T[c];
-      const R sig_f = X.c ? R(0.5) * (sigma_rc(TL, g_even(X.c, g, in, a, b, cc), ph) +
-                                      sigma_rc(TR, X.c[c], ph))
-                          : R(0.5) * (sigma_r(TL, ph) + sigma_r(TR, ph));
-      const R kap_f = R(0.5) * (g_even(kappa, g, in, a, b, cc) + kappa[c]);
-      const R jump = (alR - alL) * ih;
-      const R fn = -sig_f * kap_f * jump;
-      const R fM = R(0.5) * (g_even(MD, g, in, a, b, cc) + MD[c]);
-      us[c] = S.u[D][Tile<3>::at(tx, ty, tz)] + dt * (A + (V + fn + fM) / rho_f + ph.g[D]);
-      if (phi) phi[c] = V + fn + fM;   // the force sum before 1/rho_f (the adjoint's density term)
-    }
-  }
-  __syncthreads();
+__device__ __forceinline__ void mz_ez(const R* v, const R* Wu, const R* muu, const R* mud,
+                                      const PhysR<R>& ph, int lx, int ly, R* F) {
+  using P3 = Plane<3>;
+  using P1 = Plane<1>;
+  const int e = P1::at(lx, ly), ed = D == 0 ? P1::at(lx - 1, ly) : P1::at(lx, ly - 1);
+  const R mue = R(0.25) * (muu[e] + muu[ed] + mud[e] + mud[ed]);
+  const int w1 = P3::at(lx, ly), w0 = D == 0 ? P3::at(lx - 1, ly) : P3::at(lx, ly - 1);
+  mz_edge(v, Wu[w0], Wu[w1], mue, ph, F[0], F[1]);
+}
+
+// the forces on a D-face between cell L and cell R and the new face velocity
+template <int D, typename R>
+__device__ __forceinline__ void mz_update(const PhysR<R>& ph, bool conc, R A, R V, R alL, R alR,
+                                          R TL, R TR, R cL, R cR, R kL, R kR, R ML, R MR, R uf,
+                                          R dt, R& us, R& phi) {
+  const R ih = ph.ih;
+  const R rho_f = R(0.5) * (mixr(alL, ph.rho) + mixr(alR, ph.rho));
+  const R sig_f = conc ? R(0.5) * (sigma_rc(TL, cL, ph) + sigma_rc(TR, cR, ph))
+                       : R(0.5) * (sigma_r(TL, ph) + sigma_r(TR, ph));
+  const R kap_f = R(0.5) * (kL + kR);
+  const R jump = (alR - alL) * ih;
+  const R fn = -sig_f * kap_f * jump;
+  const R fM = R(0.5) * (ML + MR);
+  us = uf + dt * (A + (V + fn + fM) / rho_f + ph.g[D]);
+  phi = V + fn + fM;   // the force sum before 1/rho_f (the adjoint's density term)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(kZT, sizeof(R) == 4 ? 3 : 2)
     k_momentum(Geo g, PhysR<R> ph, TBC tb, Fields<R> X, const R* __restrict__ kappa,
                const R* __restrict__ M0, const R* __restrict__ M1, const R* __restrict__ M2,
                R* __restrict__ us0, R* __restrict__ us1, R* __restrict__ us2,
                const double* __restrict__ dtp, R* __restrict__ ph0, R* __restrict__ ph1,
                R* __restrict__ ph2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  MomShared<R>& S = *reinterpret_cast<MomShared<R>*>(smem_raw);
-  stage<3, F_VEL, 0>(S.u[0], X.u[0], g, tb);
-  stage<3, F_VEL, 1>(S.u[1], X.u[1], g, tb);
-  stage<3, F_VEL, 2>(S.u[2], X.u[2], g, tb);
-  stage<1, F_EVEN, 0>(S.mu, X.alpha, g, tb);
-  __syncthreads();
-  for (int e = flat_tid(); e < Tile<1>::N; e += kThreads) S.mu[e] = mixr(S.mu[e], ph.mu);
-  __syncthreads();
+  MomZ<R>& S = *reinterpret_cast<MomZ<R>*>(smem_raw);
+  using P1 = Plane<1>;
+  using P3 = Plane<3>;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * kZX + tx, j = blockIdx.y * kZY + ty;
+  const int x0 = blockIdx.x * kZX, y0 = blockIdx.y * kZY;
+  const int z0 = blockIdx.z * kZKM;
+  const int z1 = min(z0 + kZKM, nz);
+  const bool in = zcols_interior(g, 3);
+  const bool col = i < nx && j < ny;
+  const bool conc = X.c != nullptr;
   const R dt = (R)dtp[0];
-  const bool in = tile_interior(g, 3);
-  momentum_component<0>(g, ph, tb, X, kappa, M0, in, S, us0, dt, ph0);
-  momentum_component<1>(g, ph, tb, X, kappa, M1, in, S, us1, dt, ph1);
-  momentum_component<2>(g, ph, tb, X, kappa, M2, in, S, us2, dt, ph2);
+  const R ih = ph.ih;
+  // warm-up: u, v at z0-1 and z0; w at z0 and z0+1; alpha at z0-1 .. z0+1
+  for (int m = z0 - 1; m <= z0; ++m) {
+    stage_plane<3, F_VEL, 0>(S.u[mod3(m)], X.u[0], g, tb, in, m);
+    stage_plane<3, F_VEL, 1>(S.v[mod3(m)], X.u[1], g, tb, in, m);
+  }
+  for (int m = z0; m <= z0 + 1; ++m) stage_plane<3, F_VEL, 2>(S.w[mod3(m)], X.u[2], g, tb, in, m);
+  for (int m = z0 - 1; m <= z0 + 1; ++m) stage_plane<1, F_EVEN>(S.al[mod4(m)], X.alpha, g, tb, in, m);
+  __syncthreads();
+  for (int m = z0 - 1; m <= z0; ++m)
+    for (int e = tx + kZX * ty; e < P1::N; e += kZT) S.mu[mod3(m)][e] = mixr(S.al[mod4(m)][e], ph.mu);
+  __syncthreads();
+  // column windows: after the warm-up cu[0..5] = u at heights k-2 .. k+3
+  R cu[7], cv[7], cw[7];
+  R ez0[2] = {R(0), R(0)}, ez1[2] = {R(0), R(0)}, cc2[2] = {R(0), R(0)};
+  R TL2 = R(0), kL2 = R(0), cL2 = R(0), ML2 = R(0);   // the cell below the w-face
+  if (col) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      cu[m] = col_vel<0>(X.u[0], g, i, j, z0 - 3 + m);
+      cv[m] = col_vel<1>(X.u[1], g, i, j, z0 - 3 + m);
+      cw[m] = col_vel<2>(X.u[2], g, i, j, z0 - 3 + m);
+    }
+    // fluxes through the z-facing sides below plane z0
+    mz_ez<0>(cu, S.w[mod3(z0)], S.mu[mod3(z0)], S.mu[mod3(z0 - 1)], ph, tx, ty, ez0);
+    mz_ez<1>(cv, S.w[mod3(z0)], S.mu[mod3(z0)], S.mu[mod3(z0 - 1)], ph, tx, ty, ez1);
+    mz_centre_col(cw, S.mu[mod3(z0 - 1)][P1::at(tx, ty)], ph, cc2[0], cc2[1]);
+    TL2 = cell_at<F_TEMP>(X.T, g, tb, i, j, z0 - 1);
+    kL2 = cell_at<F_EVEN>(kappa, g, tb, i, j, z0 - 1);
+    if (conc) cL2 = cell_at<F_EVEN>(X.c, g, tb, i, j, z0 - 1);
+    ML2 = cell_at<F_EVEN>(M2, g, tb, i, j, z0 - 1);
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      cu[m] = cu[m + 1];
+      cv[m] = cv[m + 1];
+      cw[m] = cw[m + 1];
+    }
+  }
+  R nu = R(0), nv = R(0), nw = R(0);
+  for (int k = z0; k < z1; ++k) {
+    cp_async_wait_all();
+    __syncthreads();
+    // the slots refilled here held u, v at k - 2, w at k - 1 and alpha at
+    // k - 2, last read by the previous step
+    if (k + 1 < z1) {
+      plane_async<3, F_VEL, 0>(S.u[mod3(k + 1)], X.u[0], g, tb, in, k + 1);
+      plane_async<3, F_VEL, 1>(S.v[mod3(k + 1)], X.u[1], g, tb, in, k + 1);
+      plane_async<3, F_VEL, 2>(S.w[mod3(k + 2)], X.u[2], g, tb, in, k + 2);
+      plane_async<1, F_EVEN>(S.al[mod4(k + 2)], X.alpha, g, tb, in, k + 2);
+      cp_async_commit();
+      if (col) {
+        nu = col_vel<0>(X.u[0], g, i, j, k + 4);
+        nv = col_vel<1>(X.u[1], g, i, j, k + 4);
+        nw = col_vel<2>(X.u[2], g, i, j, k + 4);
+      }
+    }
+    // mu of plane k + 1 (alpha k + 1 arrived with the previous step's copies)
+    {
+      const R* __restrict__ a1 = S.al[mod4(k + 1)];
+      R* __restrict__ m1 = S.mu[mod3(k + 1)];
+      for (int e = tx + kZX * ty; e < P1::N; e += kZT) m1[e] = mixr(a1[e], ph.mu);
+    }
+    __syncthreads();
+    const R* __restrict__ Uk = S.u[mod3(k)];
+    const R* __restrict__ Um = S.u[mod3(k - 1)];
+    const R* __restrict__ Vk = S.v[mod3(k)];
+    const R* __restrict__ Vm = S.v[mod3(k - 1)];
+    const R* __restrict__ Wk = S.w[mod3(k)];
+    const R* __restrict__ Wp = S.w[mod3(k + 1)];
+    const R* __restrict__ mk = S.mu[mod3(k)];
+    const R* __restrict__ mm = S.mu[mod3(k - 1)];
+    const R* __restrict__ mp = S.mu[mod3(k + 1)];
+    R F[2];
+    if (col) {
+      mz_centre<0>(Uk, mk, ph, tx, ty, F[0], F[1]);
+      S.c0[0][ty][tx + 1] = F[0];
+      S.c0[1][ty][tx + 1] = F[1];
+      mz_centre<1>(Vk, mk, ph, tx, ty, F[0], F[1]);
+      S.c1[0][ty + 1][tx] = F[0];
+      S.c1[1][ty + 1][tx] = F[1];
+    }
+    if (i < nx && j <= ny) {
+      mz_e0y(Uk, Vk, mk, ph, tx, ty, F);
+      S.e0y[0][ty][tx] = F[0];
+      S.e0y[1][ty][tx] = F[1];
+      mz_e2<1>(Wk, Vk, Vm, mk, mm, ph, tx, ty, F);
+      S.e2y[0][ty][tx] = F[0];
+      S.e2y[1][ty][tx] = F[1];
+    }
+    if (i <= nx && j < ny) {
+      mz_e1x(Uk, Vk, mk, ph, tx, ty, F);
+      S.e1x[0][ty][tx] = F[0];
+      S.e1x[1][ty][tx] = F[1];
+      mz_e2<0>(Wk, Uk, Um, mk, mm, ph, tx, ty, F);
+      S.e2x[0][ty][tx] = F[0];
+      S.e2x[1][ty][tx] = F[1];
+    }
+    // the tile's high (or low) sides
+    if (ty == 0) {
+      if (i < nx && y0 + kZY <= ny) {
+        mz_e0y(Uk, Vk, mk, ph, tx, kZY, F);
+        S.e0y[0][kZY][tx] = F[0];
+        S.e0y[1][kZY][tx] = F[1];
+      }
+    } else if (ty == 1) {
+      if (i < nx) {
+        mz_centre<1>(Vk, mk, ph, tx, -1, F[0], F[1]);
+        S.c1[0][0][tx] = F[0];
+        S.c1[1][0][tx] = F[1];
+      }
+    } else if (ty == 2) {
+      if (i < nx && y0 + kZY <= ny) {
+        mz_e2<1>(Wk, Vk, Vm, mk, mm, ph, tx, kZY, F);
+        S.e2y[0][kZY][tx] = F[0];
+        S.e2y[1][kZY][tx] = F[1];
+      }
+    } else if (ty == 3) {
+      const int r = tx & 7, q = tx >> 3;
+      if (q == 0) {
+        if (y0 + r < ny) {
+          mz_centre<0>(Uk, mk, ph, -1, r, F[0], F[1]);
+          S.c0[0][r][0] = F[0];
+          S.c0[1][r][0] = F[1];
+        }
+      } else if (q == 1) {
+        if (x0 + kZX <= nx && y0 + r < ny) {
+          mz_e1x(Uk, Vk, mk, ph, kZX, r, F);
+          S.e1x[0][r][kZX] = F[0];
+          S.e1x[1][r][kZX] = F[1];
+        }
+      } else if (q == 2) {
+        if (x0 + kZX <= nx && y0 + r < ny) {
+          mz_e2<0>(Wk, Uk, Um, mk, mm, ph, kZX, r, F);
+          S.e2x[0][r][kZX] = F[0];
+          S.e2x[1][r][kZX] = F[1];
+        }
+      }
+    }
+    // z-direction fluxes above plane k
+    R ez0h[2] = {R(0), R(0)}, ez1h[2] = {R(0), R(0)}, cc2h[2] = {R(0), R(0)};
+    if (col) {
+      mz_ez<0>(cu, Wp, mp, mk, ph, tx, ty, ez0h);
+      mz_ez<1>(cv, Wp, mp, mk, ph, tx, ty, ez1h);
+      mz_centre_col(cw, mk[P1::at(tx, ty)], ph, cc2h[0], cc2h[1]);
+    }
+    __syncthreads();
+    if (col) {
+      const int c = (k * ny + j) * nx + i;
+      const R* __restrict__ ak = S.al[mod4(k)];
+      const R* __restrict__ am = S.al[mod4(k - 1)];
+      const int e1 = P1::at(tx, ty), e3 = P3::at(tx, ty);
+      const R alR = ak[e1], TR = X.T[c], kR = kappa[c], cR = conc ? X.c[c] : R(0);
+      R us, phv;
+      // u on the x-face (i, j, k)
+      if (g.bc[0] == WALL && i == 0) {
+        us0[c] = R(0);
+        if (ph0) ph0[c] = R(0);
+      } else {
+        R A = R(0) - (S.c0[0][ty][tx + 1] - S.c0[0][ty][tx]) * ih;
+        R V = R(0) + (S.c0[1][ty][tx + 1] - S.c0[1][ty][tx]) * ih;
+        A -= (S.e0y[0][ty + 1][tx] - S.e0y[0][ty][tx]) * ih;
+        V += (S.e0y[1][ty + 1][tx] - S.e0y[1][ty][tx]) * ih;
+        A -= (ez0h[0] - ez0[0]) * ih;
+        V += (ez0h[1] - ez0[1]) * ih;
+        const bool d = i >= 1;
+        const R TL = d ? X.T[c - 1] : ld_T(X.T, g, tb, i - 1, j, k);
+        const R kL = d ? kappa[c - 1] : ld_even(kappa, g, i - 1, j, k);
+        const R cL = conc ? (d ? X.c[c - 1] : ld_even(X.c, g, i - 1, j, k)) : R(0);
+        const R ML = d ? M0[c - 1] : ld_even(M0, g, i - 1, j, k);
+        mz_update<0>(ph, conc, A, V, ak[e1 - 1], alR, TL, TR, cL, cR, kL, kR, ML, M0[c], Uk[e3],
+                     dt, us, phv);
+        us0[c] = us;
+        if (ph0) ph0[c] = phv;
+      }
+      // v on the y-face (i, j, k)
+      if (g.bc[1] == WALL && j == 0) {
+        us1[c] = R(0);
+        if (ph1) ph1[c] = R(0);
+      } else {
+        R A = R(0) - (S.c1[0][ty + 1][tx] - S.c1[0][ty][tx]) * ih;
+        R V = R(0) + (S.c1[1][ty + 1][tx] - S.c1[1][ty][tx]) * ih;
+        A -= (S.e1x[0][ty][tx + 1] - S.e1x[0][ty][tx]) * ih;
+        V += (S.e1x[1][ty][tx + 1] - S.e1x[1][ty][tx]) * ih;
+        A -= (ez1h[0] - ez1[0]) * ih;
+        V += (ez1h[1] - ez1[1]) * ih;
+        const bool d = j >= 1;
+        const R TL = d ? X.T[c - nx] : ld_T(X.T, g, tb, i, j - 1, k);
+        const R kL = d ? kappa[c - nx] : ld_even(kappa, g, i, j - 1, k);
+        const R cL = conc ? (d ? X.c[c - nx] : ld_even(X.c, g, i, j - 1, k)) : R(0);
+        const R ML = d ? M1[c - nx] : ld_even(M1, g, i, j - 1, k);
+        mz_update<1>(ph, conc, A, V, ak[e1 - P1::PX], alR, TL, TR, cL, cR, kL, kR, ML, M1[c],
+                     Vk[e3], dt, us, phv);
+        us1[c] = us;
+        if (ph1) ph1[c] = phv;
+      }
+      // w on the z-face (i, j, k)
+      const R M2R = M2[c];
+      if (g.bc[2] == WALL && k == 0) {
+        us2[c] = R(0);
+        if (ph2) ph2[c] = R(0);
+      } else {
+        R A = R(0) - (cc2h[0] - cc2[0]) * ih;
+        R V = R(0) + (cc2h[1] - cc2[1]) * ih;
+        A -= (S.e2x[0][ty][tx + 1] - S.e2x[0][ty][tx]) * ih;
+        V += (S.e2x[1][ty][tx + 1] - S.e2x[1][ty][tx]) * ih;
+        A -= (S.e2y[0][ty + 1][tx] - S.e2y[0][ty][tx]) * ih;
+        V += (S.e2y[1][ty + 1][tx] - S.e2y[1][ty][tx]) * ih;
+        mz_update<2>(ph, conc, A, V, am[e1], alR, TL2, TR, cL2, cR, kL2, kR, ML2, M2R, Wk[e3], dt,
+                     us, phv);
+        us2[c] = us;
+        if (ph2) ph2[c] = phv;
+      }
+      TL2 = TR;
+      kL2 = kR;
+      cL2 = cR;
+      ML2 = M2R;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      ez0[q] = ez0h[q];
+      ez1[q] = ez1h[q];
+      cc2[q] = cc2h[q];
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      cu[m] = cu[m + 1];
+      cv[m] = cv[m + 1];
+      cw[m] = cw[m + 1];
+    }
+    cu[5] = nu;
+    cv[5] = nv;
+    cw[5] = nw;
+  }
 }
 
 template <typename R>
 void launch_momentum(const Geo& g, const Phys& ph, const TBC& tb, Fields<R> X, const R* kappa,
                      const R* M0, const R* M1, const R* M2, R* us0, R* us1, R* us2,
                      const double* dt, cudaStream_t s, R* const* phi) {
-  const int smem = (int)sizeof(MomShared<R>);
+  const int smem = (int)sizeof(MomZ<R>);
   cudaFuncSetAttribute(k_momentum<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  // float tiles (71 KB) fit three CTAs per SM when the L1/shared split favours shared memory
-  cudaFuncSetAttribute(k_momentum<R>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       cudaSharedmemCarveoutMaxShared);
-  k_momentum<R><<<tile_grid(g), dim3(kBX, kBY, kBZ), smem, s>>>(
+  k_momentum<R><<<zmarch_grid(g, kZKM), dim3(kZX, kZY), smem, s>>>(
       g, make_physr<R>(ph, g), tb, X, kappa, M0, M1, M2, us0, us1, us2, dt,
       phi ? phi[0] : nullptr, phi ? phi[1] : nullptr, phi ? phi[2] : nullptr);
 }
