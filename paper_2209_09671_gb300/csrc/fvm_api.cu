@@ -404,13 +404,21 @@ void coarsen_betas(fvm_ctx* c, MGLevel<T>* Ls) {
 }
 
 // `iters` Gauss-Seidel iterations on level l: a sweep of colour `first`,
-// then one of the other colour
+// then one of the other colour.  With `corr` (the coarse level just solved)
+// the first sweep also applies the coarse correction (k_gs_prolong), which
+// then needs no pass of its own.
 template <typename T>
-void smooth(fvm_ctx* c, MGLevel<T>& L, int l, int iters, int first) {
+void smooth(fvm_ctx* c, MGLevel<T>& L, int l, int iters, int first,
+            const MGLevel<T>* corr = nullptr) {
   const int kg = l == 0 ? FVM_K_GS_FINE : FVM_K_GS_COARSE;
   for (int q = 0; q < iters; ++q) {
-    for (int col = 0; col < 2; ++col)
-      TIMED(c, kg, 1, launch_gs<T>(L, col == 0 ? first : 1 - first, c->stream));
+    for (int col = 0; col < 2; ++col) {
+      const int colour = col == 0 ? first : 1 - first;
+      if (q == 0 && col == 0 && corr)
+        TIMED(c, kg, 1, launch_gs_prolong<T>(L, *corr, colour, c->stream));
+      else
+        TIMED(c, kg, 1, launch_gs<T>(L, colour, c->stream));
+    }
   }
 }
 
@@ -462,9 +470,14 @@ void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
   TIMED(c, l == 0 ? FVM_K_RESTRICT_FINE : FVM_K_RESTRICT_COARSE, 1,
         launch_residual_restrict<T>(Ls[l], Ls[l + 1], s));
   vcycle<T>(c, Ls, l + 1, coarse_rtol);
-  TIMED(c, l == 0 ? FVM_K_PROLONG_FINE : FVM_K_PROLONG_COARSE, 1,
-        launch_prolong<T>(Ls[l], Ls[l + 1], s));
-  smooth<T>(c, Ls[l], l, l == 0 ? c->prm.mg_post : coarse_post(c), 1);
+  const int post = l == 0 ? c->prm.mg_post : coarse_post(c);
+  if (post > 0) {
+    // the prolongation rides on the first post-smoothing sweep
+    smooth<T>(c, Ls[l], l, post, 1, &Ls[l + 1]);
+  } else {
+    TIMED(c, l == 0 ? FVM_K_PROLONG_FINE : FVM_K_PROLONG_COARSE, 1,
+          launch_prolong<T>(Ls[l], Ls[l + 1], s));
+  }
 }
 
 // F64: L p = b (b mean-free, double), beta0 already computed

@@ -144,6 +144,10 @@ template <typename T>
 void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
 template <typename T>
 void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
+// a sweep of `colour` on F reading the other colour plus the coarse
+// correction C.x of its parent cells (the prolongation folded into the sweep)
+template <typename T>
+void launch_gs_prolong(const MGLevel<T>& F, const MGLevel<T>& C, int colour, cudaStream_t s);
 template <typename T>
 void launch_beta_coarsen(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
 // The coarse tail of a V-cycle (levels of at most kTailCells cells, the

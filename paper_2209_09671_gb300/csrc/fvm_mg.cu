@@ -4,6 +4,7 @@
 //   k_gs                red-black Gauss-Seidel sweep of one colour (i+j+k mod 2)
 //   k_residual_restrict residual on the fine level, mean over the children
 //   k_prolong           piecewise-constant prolongation, added to the fine level
+//   k_gs_prolong        the first sweep after the correction with the prolongation folded in
 //   k_beta_coarsen      coarse face beta = mean of the fine faces it covers
 //   k_coarse_cg         conjugate gradients on the coarsest level, one CTA
 //   k_residual_norm2    ||b - L x||^2 partial sums
@@ -150,6 +151,23 @@ __device__ __forceinline__ void decode_lv(const Geo& g, long long c, int& i, int
 }
 
 // ---------------------------------------------------------------------------
+// Gauss-Seidel value of one cell from its right-hand side, the face betas
+// and the neighbour values on the low and high side of each axis (axes of
+// one cell carry no coupling)
+template <typename T>
+__device__ __forceinline__ T gs_formula(const Geo& g, const T* w, T b, const T* blo, const T* bhi,
+                                        const T* xlo, const T* xhi) {
+  T num = b;
+  T den = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (g.n[d] == 1) continue;
+    num += (blo[d] * xlo[d] + bhi[d] * xhi[d]) * w[d];
+    den += (blo[d] + bhi[d]) * w[d];
+  }
+  return num / den;
+}
+
 // Gauss-Seidel update of one cell (its colour's neighbours are fixed)
 template <typename T>
 __device__ __forceinline__ void gs_point(const MGLevel<T>& L, int i, int j, int k) {
@@ -157,16 +175,13 @@ __device__ __forceinline__ void gs_point(const MGLevel<T>& L, int i, int j, int 
   const int c = (k * g.n[1] + j) * g.n[0] + i;
   OpNb<T> nb;
   neighbours(L, i, j, k, c, nb);
-  T num = L.b[c];
-  T den = T(0);
+  T xlo[3], xhi[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    if (g.n[d] == 1) continue;
-    const T w = L.w[d];
-    num += (nb.blo[d] * L.x[nb.lo[d]] + nb.bhi[d] * L.x[nb.hi[d]]) * w;
-    den += (nb.blo[d] + nb.bhi[d]) * w;
+    xlo[d] = L.x[nb.lo[d]];
+    xhi[d] = L.x[nb.hi[d]];
   }
-  L.x[c] = num / den;
+  L.x[c] = gs_formula(g, L.w, L.b[c], nb.blo, nb.bhi, xlo, xhi);
 }
 
 template <typename T>
@@ -270,6 +285,51 @@ void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s) {
   const dim3 bs(32, 4, 2);
   const dim3 gs((F.geo.n[0] + 31) / 32, (F.geo.n[1] + 3) / 4, (F.geo.n[2] + 1) / 2);
   k_prolong<T><<<gs, bs, 0, s>>>(F, C);
+}
+
+// The first colour sweep after the coarse correction with the
+// piecewise-constant prolongation folded in.  A sweep of one colour reads
+// only the other colour, so it takes those cells' values plus the coarse
+// correction of their parent cells on the fly; the other colour's stored
+// values are then overwritten by the next sweep without being read.  The
+// pair of sweeps therefore leaves x as k_prolong followed by two k_gs
+// launches would, bit for bit, without the prolongation's pass over x.
+template <typename T>
+__global__ void k_gs_prolong(MGLevel<T> F, MGLevel<T> C, int colour) {
+  const Geo& g = F.geo;
+  const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (j >= g.n[1] || k >= g.n[2]) return;
+  const int i = 2 * i2 + ((colour + j + k) & 1);
+  if (i >= g.n[0]) return;
+  const int c = (k * g.n[1] + j) * g.n[0] + i;
+  OpNb<T> nb;
+  neighbours(F, i, j, k, c, nb);
+  const int idx[3] = {i, j, k};
+  T xlo[3], xhi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int n = g.n[d];
+    int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+    lo[d] = idx[d] == 0 ? n - 1 : idx[d] - 1;
+    hi[d] = idx[d] == n - 1 ? 0 : idx[d] + 1;
+    const long long pl = lin(C.geo, coarse_index(lo[0], F.f[0]), coarse_index(lo[1], F.f[1]),
+                             coarse_index(lo[2], F.f[2]));
+    const long long ph = lin(C.geo, coarse_index(hi[0], F.f[0]), coarse_index(hi[1], F.f[1]),
+                             coarse_index(hi[2], F.f[2]));
+    xlo[d] = F.x[nb.lo[d]] + C.x[pl];
+    xhi[d] = F.x[nb.hi[d]] + C.x[ph];
+  }
+  F.x[c] = gs_formula(g, F.w, F.b[c], nb.blo, nb.bhi, xlo, xhi);
+}
+
+template <typename T>
+void launch_gs_prolong(const MGLevel<T>& F, const MGLevel<T>& C, int colour, cudaStream_t s) {
+  const int hx = (F.geo.n[0] + 1) / 2;
+  dim3 bs(32, 4, 2);
+  dim3 gs((hx + 31) / 32, (F.geo.n[1] + 3) / 4, (F.geo.n[2] + 1) / 2);
+  k_gs_prolong<T><<<gs, bs, 0, s>>>(F, C, colour);
 }
 
 template <typename T>
@@ -406,20 +466,35 @@ __global__ void __launch_bounds__(1024) k_coarse_cg(MGLevel<T> L, double* __rest
 // post-sweeps black first), separated by block barriers; within one colour
 // sweep (and within restriction and prolongation) the points are
 // independent, so the result equals that of the per-level kernels bit for bit.
+// one colour sweep of a tail level by the CTA: thread t takes the t-th cell
+// of the colour (rows of ceil(nx/2) such cells); the row and plane indices
+// come from float reciprocals, exact for the at most 4096 cells of a tail
+// level, instead of integer divisions
+template <typename T>
+__device__ __forceinline__ void tail_colour(const MGLevel<T>& L, int col) {
+  const Geo& g = L.geo;
+  const int hx = (g.n[0] + 1) >> 1;
+  const int half = hx * g.n[1] * g.n[2];
+  const float ihx = 1.0f / (float)hx, iny = 1.0f / (float)g.n[1];
+  for (int t = threadIdx.x; t < half; t += blockDim.x) {
+    const int q = (int)(((float)t + 0.5f) * ihx);   // row j + ny k
+    const int i2 = t - q * hx;
+    const int k = (int)(((float)q + 0.5f) * iny);
+    const int j = q - k * g.n[1];
+    const int i = 2 * i2 + ((col + j + k) & 1);
+    if (i < g.n[0]) gs_point(L, i, j, k);
+  }
+}
+
 template <typename T>
 __device__ void tail_body(const MGLevel<T>* Ls, int nl, double* r, double* d, double* Ad,
                           double rtol, int maxit, int pre, int post, double* sh, CgSmem& cs) {
   const int last = nl - 1;
   for (int l = 0; l < last; ++l) {
     const MGLevel<T>& L = Ls[l];
-    const Geo& g = L.geo;
     for (int it = 0; it < pre; ++it)
       for (int col = 0; col < 2; ++col) {
-        for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) {
-          int i, j, k;
-          decode_lv(g, c, i, j, k);
-          if (((i + j + k) & 1) == col) gs_point(L, i, j, k);
-        }
+        tail_colour(L, col);
         __syncthreads();
       }
     for (int cc = threadIdx.x; cc < (int)Ls[l + 1].geo.N; cc += blockDim.x)
@@ -435,11 +510,7 @@ __device__ void tail_body(const MGLevel<T>* Ls, int nl, double* r, double* d, do
     __syncthreads();
     for (int it = 0; it < post; ++it)
       for (int col = 0; col < 2; ++col) {
-        for (int c = threadIdx.x; c < (int)g.N; c += blockDim.x) {
-          int i, j, k;
-          decode_lv(g, c, i, j, k);
-          if (((i + j + k) & 1) == 1 - col) gs_point(L, i, j, k);
-        }
+        tail_colour(L, 1 - col);
         __syncthreads();
       }
   }
@@ -629,6 +700,7 @@ void launch_ctl_store(const SolveCtl* ctl, SolveCtl* rec, int* sticky, cudaStrea
   template void launch_residual_restrict<T>(const MGLevel<T>&, const MGLevel<T>&,            \
                                             cudaStream_t);                                   \
   template void launch_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);       \
+  template void launch_gs_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, int, cudaStream_t); \
   template void launch_beta_coarsen<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);  \
   template void launch_coarse_tail<T>(const TailArgs<T>&, cudaStream_t);                     \
   template void launch_coarse_cg<T>(const MGLevel<T>&, double*, double*, double*, double,  \
