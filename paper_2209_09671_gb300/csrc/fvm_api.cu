@@ -403,22 +403,39 @@ void coarsen_betas(fvm_ctx* c, MGLevel<T>* Ls) {
     TIMED(c, FVM_K_BETA, 1, launch_beta_coarsen<T>(Ls[l], Ls[l + 1], c->stream));
 }
 
+// what the sweeps of one smoothing step fold in
+template <typename T>
+struct SweepFold {
+  const MGLevel<T>* corr = nullptr;   // first sweep: the coarse correction of this level (prolongation)
+  bool zero = false;                  // first sweep: x starts at 0 (zeroes the other colour)
+  double* addp = nullptr;             // last sweep: p += x (the mixed form's float level 0)
+};
+
+inline void addp_sweep(fvm_ctx* c, int kg, const MGLevel<float>& L, int colour, double* p) {
+  TIMED(c, kg, 1, launch_gs_addp(L, colour, p, c->stream));
+}
+inline void addp_sweep(fvm_ctx*, int, const MGLevel<double>&, int, double*) {}
+
 // `iters` Gauss-Seidel iterations on level l: a sweep of colour `first`,
-// then one of the other colour.  With `corr` (the coarse level just solved)
-// the first sweep also applies the coarse correction (k_gs_prolong), which
-// then needs no pass of its own.
+// then one of the other colour.  The first sweep can apply the coarse
+// correction (k_gs_prolong) or start from x = 0 (k_gs_zero), the last one can
+// add x to p (k_gs_addp): each replaces a pass of its own over x, with the
+// same numbers.
 template <typename T>
 void smooth(fvm_ctx* c, MGLevel<T>& L, int l, int iters, int first,
-            const MGLevel<T>* corr = nullptr) {
+            const SweepFold<T>& f = SweepFold<T>()) {
   const int kg = l == 0 ? FVM_K_GS_FINE : FVM_K_GS_COARSE;
-  for (int q = 0; q < iters; ++q) {
-    for (int col = 0; col < 2; ++col) {
-      const int colour = col == 0 ? first : 1 - first;
-      if (q == 0 && col == 0 && corr)
-        TIMED(c, kg, 1, launch_gs_prolong<T>(L, *corr, colour, c->stream));
-      else
-        TIMED(c, kg, 1, launch_gs<T>(L, colour, c->stream));
-    }
+  const int last = 2 * iters - 1;
+  for (int t = 0; t <= last; ++t) {
+    const int colour = (t & 1) == 0 ? first : 1 - first;
+    if (t == 0 && f.corr)
+      TIMED(c, kg, 1, launch_gs_prolong<T>(L, *f.corr, colour, c->stream));
+    else if (t == 0 && f.zero)
+      TIMED(c, kg, 1, launch_gs_zero<T>(L, colour, c->stream));
+    else if (t == last && f.addp)
+      addp_sweep(c, kg, L, colour, f.addp);
+    else
+      TIMED(c, kg, 1, launch_gs<T>(L, colour, c->stream));
   }
 }
 
@@ -444,9 +461,19 @@ int tail_start(const fvm_ctx* c) {
 // V(pre, post) cycle: red-black sweeps before the coarse correction,
 // black-red after, CG on the coarsest level; the levels from tail_start()
 // down run in one kernel
+// zero: level l's x starts at 0 (not yet zeroed); addp: add level 0's x to p
+// at the end (float only)
 template <typename T>
-void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
+void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol, bool zero = false,
+            double* addp = nullptr) {
   cudaStream_t s = c->stream;
+  const int pre = l == 0 ? c->prm.mg_pre : coarse_pre(c);
+  const int post = l == 0 ? c->prm.mg_post : coarse_post(c);
+  const bool whole = l == tail_start(c) || l == c->nlev - 1;   // no sweeps of its own here
+  if (zero && (whole || pre == 0))
+    TIMED(c, FVM_K_MISC, 1, launch_zero<T>(Ls[l].x, Ls[l].geo.N, s));
+  const bool fold_zero = zero && !whole && pre > 0;
+  const bool fold_add = addp && !whole && post > 0;
   if (l == tail_start(c)) {
     TailArgs<T> A;
     A.nl = c->nlev - l;
@@ -459,25 +486,29 @@ void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol) {
     A.pre = coarse_pre(c);
     A.post = coarse_post(c);
     TIMED(c, FVM_K_COARSE_TAIL, 1, launch_coarse_tail<T>(A, s));
-    return;
-  }
-  if (l == c->nlev - 1) {
+  } else if (l == c->nlev - 1) {
     TIMED(c, FVM_K_COARSE_CG, 1, launch_coarse_cg<T>(Ls[l], (double*)c->cg[0], (double*)c->cg[1], (double*)c->cg[2],
                                                    coarse_rtol, c->prm.coarse_maxit, s));
-    return;
-  }
-  smooth<T>(c, Ls[l], l, l == 0 ? c->prm.mg_pre : coarse_pre(c), 0);
-  TIMED(c, l == 0 ? FVM_K_RESTRICT_FINE : FVM_K_RESTRICT_COARSE, 1,
-        launch_residual_restrict<T>(Ls[l], Ls[l + 1], s));
-  vcycle<T>(c, Ls, l + 1, coarse_rtol);
-  const int post = l == 0 ? c->prm.mg_post : coarse_post(c);
-  if (post > 0) {
-    // the prolongation rides on the first post-smoothing sweep
-    smooth<T>(c, Ls[l], l, post, 1, &Ls[l + 1]);
   } else {
-    TIMED(c, l == 0 ? FVM_K_PROLONG_FINE : FVM_K_PROLONG_COARSE, 1,
-          launch_prolong<T>(Ls[l], Ls[l + 1], s));
+    SweepFold<T> fpre;
+    fpre.zero = fold_zero;
+    smooth<T>(c, Ls[l], l, pre, 0, fpre);
+    TIMED(c, l == 0 ? FVM_K_RESTRICT_FINE : FVM_K_RESTRICT_COARSE, 1,
+          launch_residual_restrict<T>(Ls[l], Ls[l + 1], s));
+    vcycle<T>(c, Ls, l + 1, coarse_rtol);
+    if (post > 0) {
+      // the prolongation rides on the first post-smoothing sweep
+      SweepFold<T> fpost;
+      fpost.corr = &Ls[l + 1];
+      fpost.addp = fold_add ? addp : nullptr;
+      smooth<T>(c, Ls[l], l, post, 1, fpost);
+    } else {
+      TIMED(c, l == 0 ? FVM_K_PROLONG_FINE : FVM_K_PROLONG_COARSE, 1,
+            launch_prolong<T>(Ls[l], Ls[l + 1], s));
+    }
   }
+  if (addp && !fold_add)
+    TIMED(c, FVM_K_ADD_CORRECTION, 1, launch_add_correction(Ls[0].geo.N, addp, (const float*)Ls[0].x, s));
 }
 
 // F64: L p = b (b mean-free, double), beta0 already computed
@@ -546,9 +577,11 @@ void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, 
                  float* const* be, double crtol) {
   cudaStream_t s = c->stream;
   const long long N = c->g.N;
-  TIMED(c, FVM_K_MISC, 1, launch_zero<float>(c->e32, N, s));
-  for (int q = 0; q < c->prm.mx_inner_cycles; ++q) vcycle<float>(c, Ls, 0, crtol);
-  TIMED(c, FVM_K_ADD_CORRECTION, 1, launch_add_correction(N, p, c->e32, s));
+  // e = 0, the inner cycles and p += e: the zeroing rides on the first sweep
+  // of the first cycle, the addition on the last sweep of the last one
+  const int m = c->prm.mx_inner_cycles;
+  for (int q = 0; q < m; ++q) vcycle<float>(c, Ls, 0, crtol, q == 0, q == m - 1 ? p : nullptr);
+  (void)N;
   TIMED(c, FVM_K_RESIDUAL64, 2, launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, s));
 }
 

@@ -148,6 +148,12 @@ void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
 // correction C.x of its parent cells (the prolongation folded into the sweep)
 template <typename T>
 void launch_gs_prolong(const MGLevel<T>& F, const MGLevel<T>& C, int colour, cudaStream_t s);
+// a sweep of `colour` from x = 0 that also zeroes the other colour
+template <typename T>
+void launch_gs_zero(const MGLevel<T>& L, int colour, cudaStream_t s);
+// a float sweep of `colour` that adds the new values of its cells and the
+// values of the other colour to the double p (p += x after the sweep)
+void launch_gs_addp(const MGLevel<float>& L, int colour, double* p, cudaStream_t s);
 template <typename T>
 void launch_beta_coarsen(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
 // The coarse tail of a V-cycle (levels of at most kTailCells cells, the

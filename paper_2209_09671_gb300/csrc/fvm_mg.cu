@@ -5,6 +5,7 @@
 //   k_residual_restrict residual on the fine level, mean over the children
 //   k_prolong           piecewise-constant prolongation, added to the fine level
 //   k_gs_prolong        the first sweep after the correction with the prolongation folded in
+//   k_gs_zero, k_gs_addp the first sweep from x = 0 and the last one adding x to p (mixed form)
 //   k_beta_coarsen      coarse face beta = mean of the fine faces it covers
 //   k_coarse_cg         conjugate gradients on the coarsest level, one CTA
 //   k_residual_norm2    ||b - L x||^2 partial sums
@@ -322,6 +323,70 @@ __global__ void k_gs_prolong(MGLevel<T> F, MGLevel<T> C, int colour) {
     xhi[d] = F.x[nb.hi[d]] + C.x[ph];
   }
   F.x[c] = gs_formula(g, F.w, F.b[c], nb.blo, nb.bhi, xlo, xhi);
+}
+
+// The first sweep of a solve that starts from x = 0 (the mixed form's inner
+// correction): the other colour's values are 0, so the swept cells take
+// gs_formula with zero neighbours and the cells of the other colour are set
+// to 0 by the same thread (the pair 2 i2, 2 i2 + 1 of its row), which
+// replaces zeroing x in a pass of its own.
+template <typename T>
+__global__ void k_gs_zero(MGLevel<T> L, int colour) {
+  const Geo& g = L.geo;
+  const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (j >= g.n[1] || k >= g.n[2]) return;
+  const int i = 2 * i2 + ((colour + j + k) & 1), io = i ^ 1;
+  const int row = (k * g.n[1] + j) * g.n[0];
+  if (io < g.n[0]) L.x[row + io] = T(0);
+  if (i >= g.n[0]) return;
+  OpNb<T> nb;
+  neighbours(L, i, j, k, row + i, nb);
+  const T z[3] = {T(0), T(0), T(0)};
+  L.x[row + i] = gs_formula(g, L.w, L.b[row + i], nb.blo, nb.bhi, z, z);
+}
+
+// The last sweep of the mixed form's inner correction with p += e folded in:
+// the thread adds the new value of its cell and the final value of the other
+// colour's cell beside it (not written in this sweep) to the double p.  The
+// correction e itself is not stored again; the next refinement starts it
+// from 0.
+__global__ void k_gs_addp(MGLevel<float> L, int colour, double* __restrict__ p) {
+  const Geo& g = L.geo;
+  const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z * blockDim.z + threadIdx.z;
+  if (j >= g.n[1] || k >= g.n[2]) return;
+  const int i = 2 * i2 + ((colour + j + k) & 1), io = i ^ 1;
+  const int row = (k * g.n[1] + j) * g.n[0];
+  if (io < g.n[0]) p[row + io] = p[row + io] + (double)L.x[row + io];
+  if (i >= g.n[0]) return;
+  OpNb<float> nb;
+  neighbours(L, i, j, k, row + i, nb);
+  float xlo[3], xhi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    xlo[d] = L.x[nb.lo[d]];
+    xhi[d] = L.x[nb.hi[d]];
+  }
+  const float e = gs_formula(g, L.w, L.b[row + i], nb.blo, nb.bhi, xlo, xhi);
+  p[row + i] = p[row + i] + (double)e;
+}
+
+template <typename T>
+void launch_gs_zero(const MGLevel<T>& L, int colour, cudaStream_t s) {
+  const int hx = (L.geo.n[0] + 1) / 2;
+  dim3 bs(32, 4, 2);
+  dim3 gs((hx + 31) / 32, (L.geo.n[1] + 3) / 4, (L.geo.n[2] + 1) / 2);
+  k_gs_zero<T><<<gs, bs, 0, s>>>(L, colour);
+}
+
+void launch_gs_addp(const MGLevel<float>& L, int colour, double* p, cudaStream_t s) {
+  const int hx = (L.geo.n[0] + 1) / 2;
+  dim3 bs(32, 4, 2);
+  dim3 gs((hx + 31) / 32, (L.geo.n[1] + 3) / 4, (L.geo.n[2] + 1) / 2);
+  k_gs_addp<<<gs, bs, 0, s>>>(L, colour, p);
 }
 
 template <typename T>
@@ -701,6 +766,7 @@ void launch_ctl_store(const SolveCtl* ctl, SolveCtl* rec, int* sticky, cudaStrea
                                             cudaStream_t);                                   \
   template void launch_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);       \
   template void launch_gs_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, int, cudaStream_t); \
+  template void launch_gs_zero<T>(const MGLevel<T>&, int, cudaStream_t);                      \
   template void launch_beta_coarsen<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);  \
   template void launch_coarse_tail<T>(const TailArgs<T>&, cudaStream_t);                     \
   template void launch_coarse_cg<T>(const MGLevel<T>&, double*, double*, double*, double,  \
