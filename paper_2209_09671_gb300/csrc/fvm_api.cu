@@ -408,6 +408,7 @@ template <typename T>
 struct SweepFold {
   const MGLevel<T>* corr = nullptr;   // first sweep: the coarse correction of this level (prolongation)
   bool zero = false;                  // first sweep: x starts at 0 (zeroes the other colour)
+  bool skip_first = false;            // first sweep: already taken (by k_residual64)
   double* addp = nullptr;             // last sweep: p += x (the mixed form's float level 0)
 };
 
@@ -428,6 +429,7 @@ void smooth(fvm_ctx* c, MGLevel<T>& L, int l, int iters, int first,
   const int last = 2 * iters - 1;
   for (int t = 0; t <= last; ++t) {
     const int colour = (t & 1) == 0 ? first : 1 - first;
+    if (t == 0 && f.skip_first) continue;
     if (t == 0 && f.corr)
       TIMED(c, kg, 1, launch_gs_prolong<T>(L, *f.corr, colour, c->stream));
     else if (t == 0 && f.zero)
@@ -461,15 +463,36 @@ int tail_start(const fvm_ctx* c) {
 // V(pre, post) cycle: red-black sweeps before the coarse correction,
 // black-red after, CG on the coarsest level; the levels from tail_start()
 // down run in one kernel
-// zero: level l's x starts at 0 (not yet zeroed); addp: add level 0's x to p
-// at the end (float only)
+// How the finest level's x starts: as it is, at 0 (not yet zeroed), or with
+// the first sweep from 0 already taken by k_residual64 (mixed form).
+enum { kStartAsIs = 0, kStartZero = 1, kStartFirstSwept = 2 };
+
+// the mixed form's residual kernel takes the first sweep of each inner solve
+// when that solve begins with a sweep on a finest level of its own
+bool residual_takes_first_sweep(const fvm_ctx* c) {
+  return c->prm.mg_pre > 0 && c->nlev > 1 && c->prm.mx_inner_cycles > 0;
+}
+
+// the residual r = b - L p (double, stored as float) of the mixed form, with
+// the next inner solve's first sweep when residual_takes_first_sweep()
+void mixed_residual(fvm_ctx* c, double* p, const double* b, float* const* be) {
+  const bool f = residual_takes_first_sweep(c);
+  const float w32[3] = {(float)c->g.w[0], (float)c->g.w[1], (float)c->g.w[2]};
+  TIMED(c, FVM_K_RESIDUAL64, 2,
+        launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, c->stream,
+                          f ? c->e32 : nullptr, w32));
+}
+
+// start: how level l's x starts (kStart*); addp: add level 0's x to p at the
+// end (float only)
 template <typename T>
-void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol, bool zero = false,
+void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol, int start = kStartAsIs,
             double* addp = nullptr) {
   cudaStream_t s = c->stream;
   const int pre = l == 0 ? c->prm.mg_pre : coarse_pre(c);
   const int post = l == 0 ? c->prm.mg_post : coarse_post(c);
   const bool whole = l == tail_start(c) || l == c->nlev - 1;   // no sweeps of its own here
+  const bool zero = start == kStartZero;
   if (zero && (whole || pre == 0))
     TIMED(c, FVM_K_MISC, 1, launch_zero<T>(Ls[l].x, Ls[l].geo.N, s));
   const bool fold_zero = zero && !whole && pre > 0;
@@ -492,6 +515,7 @@ void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol, bool zero = f
   } else {
     SweepFold<T> fpre;
     fpre.zero = fold_zero;
+    fpre.skip_first = start == kStartFirstSwept;
     smooth<T>(c, Ls[l], l, pre, 0, fpre);
     TIMED(c, l == 0 ? FVM_K_RESTRICT_FINE : FVM_K_RESTRICT_COARSE, 1,
           launch_residual_restrict<T>(Ls[l], Ls[l + 1], s));
@@ -580,9 +604,12 @@ void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, 
   // e = 0, the inner cycles and p += e: the zeroing rides on the first sweep
   // of the first cycle, the addition on the last sweep of the last one
   const int m = c->prm.mx_inner_cycles;
-  for (int q = 0; q < m; ++q) vcycle<float>(c, Ls, 0, crtol, q == 0, q == m - 1 ? p : nullptr);
+  const int start0 = residual_takes_first_sweep(c) ? kStartFirstSwept : kStartZero;
+  for (int q = 0; q < m; ++q)
+    vcycle<float>(c, Ls, 0, crtol, q == 0 ? start0 : kStartAsIs, q == m - 1 ? p : nullptr);
   (void)N;
-  TIMED(c, FVM_K_RESIDUAL64, 2, launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, s));
+  (void)s;
+  mixed_residual(c, p, b, be);
 }
 
 fvm_status solve_mixed(fvm_ctx* c, const float* alpha, double* p, double* b, int* cycles_out,
@@ -610,7 +637,7 @@ fvm_status solve_mixed(fvm_ctx* c, const float* alpha, double* p, double* b, int
   const double crtol = c->prm.coarse_rtol > 1e-6 ? c->prm.coarse_rtol : 1e-6;
   int outer = 0;
   double rel = 0.0;
-  TIMED(c, FVM_K_RESIDUAL64, 2, launch_residual64(c->g, p, b, be, c->r32, c->partial, c->scal + 1, s));
+  mixed_residual(c, p, b, be);
   for (;;) {
     if (fixed > 0) {
       if (outer == fixed) {
@@ -660,8 +687,7 @@ void graph_prologue(fvm_ctx* c, double* p, cudaGraphConditionalHandle h) {
     coarsen_betas<float>(c, Ls);
     TIMED(c, FVM_K_MISC, 1, launch_ctl_reset(c->ctl, s));
     TIMED(c, FVM_K_MISC, 2, launch_sum_field<double>(c->b, N, true, c->partial, c->scal + 0, s));
-    TIMED(c, FVM_K_RESIDUAL64, 2,
-          launch_residual64(c->g, p, c->b, be, c->r32, c->partial, c->scal + 1, s));
+    mixed_residual(c, p, c->b, be);
   } else {
     MGLevel<double> Ls[kMaxLevels];
     double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};

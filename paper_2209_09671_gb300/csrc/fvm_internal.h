@@ -179,7 +179,8 @@ template <typename T>
 void launch_residual_norm2(const MGLevel<T>& L, double* partial, double* out, cudaStream_t s);
 // Mixed form: r = b - L p in double with float beta; writes r32 and ||r||^2
 void launch_residual64(const Geo& g, const double* p, const double* b, float* const* beta,
-                       float* r32, double* partial, double* out, cudaStream_t s);
+                       float* r32, double* partial, double* out, cudaStream_t s,
+                       float* e32 = nullptr, const float* w32 = nullptr);
 void launch_add_correction(long long n, double* p, const float* e, cudaStream_t s);
 
 // ----- device-side control of the pressure solve (fvm_mg.cu) -----------------

@@ -17,6 +17,11 @@
 
 namespace fvm {
 
+// three float weights passed by value to a kernel
+struct W3 {
+  float w[3];
+};
+
 static inline unsigned grid1d(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -635,10 +640,14 @@ __device__ __forceinline__ double beta_to_double(float f) {
   return mag == 0u ? 0.0 : __hiloint2double((int)hi, (int)lo);
 }
 
+// With e32: the first Gauss-Seidel sweep of the next inner solve (colour 0
+// from e = 0, the other colour 0) is taken here, from the float residual just
+// stored, with the same arithmetic as k_gs_zero: the inner solve then starts
+// at its second sweep.  w32: the finest level's float 1/h^2 per axis.
 __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* __restrict__ b,
                              const float* __restrict__ b0, const float* __restrict__ b1,
                              const float* __restrict__ b2, float* __restrict__ r32,
-                             double* __restrict__ partial) {
+                             double* __restrict__ partial, float* __restrict__ e32, W3 w32) {
   __shared__ double sh[33];
   const float* be[3] = {b0, b1, b2};
   const int st[3] = {1, g.n[0], g.n[0] * g.n[1]};
@@ -651,6 +660,7 @@ __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* 
     decode_lv(g, c, i, j, k);
     const int idx[3] = {i, j, k};
     const double pc = p[c];
+    float blo[3] = {0.f, 0.f, 0.f}, bhi[3] = {0.f, 0.f, 0.f};
     // the fine level has cubic cells: one weight 1/h^2 for every coupled axis
     double lsum = 0.0;
 #pragma unroll
@@ -659,13 +669,18 @@ __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* 
       if (n == 1) continue;
       const int clo = idx[d] == 0 ? c + (n - 1) * st[d] : c - st[d];
       const int chi = idx[d] == n - 1 ? c - (n - 1) * st[d] : c + st[d];
-      const float blo = be[d][c];
-      const float bhi = (g.bc[d] == WALL && idx[d] == n - 1) ? 0.f : be[d][chi];
-      lsum = fma(beta_to_double(blo), pc - p[clo], lsum);
-      lsum = fma(beta_to_double(bhi), pc - p[chi], lsum);
+      blo[d] = be[d][c];
+      bhi[d] = (g.bc[d] == WALL && idx[d] == n - 1) ? 0.f : be[d][chi];
+      lsum = fma(beta_to_double(blo[d]), pc - p[clo], lsum);
+      lsum = fma(beta_to_double(bhi[d]), pc - p[chi], lsum);
     }
     const double r = fma(-wu, lsum, b[c]);
-    r32[c] = (float)r;
+    const float rf = (float)r;
+    r32[c] = rf;
+    if (e32) {
+      const float z[3] = {0.f, 0.f, 0.f};
+      e32[c] = ((i + j + k) & 1) == 0 ? gs_formula(g, w32.w, rf, blo, bhi, z, z) : 0.f;
+    }
     acc += r * r;
   }
   double s = block_sum_all(acc, sh);
@@ -673,8 +688,12 @@ __global__ void k_residual64(Geo g, const double* __restrict__ p, const double* 
 }
 
 void launch_residual64(const Geo& g, const double* p, const double* b, float* const* beta,
-                       float* r32, double* partial, double* out, cudaStream_t s) {
-  k_residual64<<<kRedBlocks, 256, 0, s>>>(g, p, b, beta[0], beta[1], beta[2], r32, partial);
+                       float* r32, double* partial, double* out, cudaStream_t s, float* e32,
+                       const float* w32) {
+  W3 w = {{0.f, 0.f, 0.f}};
+  if (w32)
+    for (int d = 0; d < 3; ++d) w.w[d] = w32[d];
+  k_residual64<<<kRedBlocks, 256, 0, s>>>(g, p, b, beta[0], beta[1], beta[2], r32, partial, e32, w);
   launch_sum_partials(partial, kRedBlocks, out, s);
 }
 
