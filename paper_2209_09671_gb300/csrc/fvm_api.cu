@@ -517,9 +517,12 @@ void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol, int start = k
     fpre.zero = fold_zero;
     fpre.skip_first = start == kStartFirstSwept;
     smooth<T>(c, Ls[l], l, pre, 0, fpre);
+    // the next level's first sweep rides on the restriction when that level
+    // sweeps on its own (not the tail, not the coarsest)
+    const bool swept = l + 1 != tail_start(c) && l + 1 != c->nlev - 1 && coarse_pre(c) > 0;
     TIMED(c, l == 0 ? FVM_K_RESTRICT_FINE : FVM_K_RESTRICT_COARSE, 1,
-          launch_residual_restrict<T>(Ls[l], Ls[l + 1], s));
-    vcycle<T>(c, Ls, l + 1, coarse_rtol);
+          launch_residual_restrict<T>(Ls[l], Ls[l + 1], s, swept));
+    vcycle<T>(c, Ls, l + 1, coarse_rtol, swept ? kStartFirstSwept : kStartAsIs);
     if (post > 0) {
       // the prolongation rides on the first post-smoothing sweep
       SweepFold<T> fpost;

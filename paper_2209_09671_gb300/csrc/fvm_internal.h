@@ -141,7 +141,8 @@ void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s);
 
 
 template <typename T>
-void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
+void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s,
+                              bool sweep = false);
 template <typename T>
 void launch_prolong(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s);
 // a sweep of `colour` on F reading the other colour plus the coarse

@@ -241,19 +241,29 @@ __device__ __forceinline__ void restrict_point(const MGLevel<T>& F, const MGLeve
 
 // one thread per coarse cell on a 3D grid (no index division per thread)
 template <typename T>
-__global__ void k_residual_restrict(MGLevel<T> F, MGLevel<T> C) {
+__global__ void k_residual_restrict(MGLevel<T> F, MGLevel<T> C, int sweep) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int K = blockIdx.z * blockDim.z + threadIdx.z;
   if (I >= C.geo.n[0] || J >= C.geo.n[1] || K >= C.geo.n[2]) return;
   restrict_point(F, C, I, J, K);
+  if (sweep && ((I + J + K) & 1) == 0) {
+    // the coarse level's first sweep (colour 0 from x = 0) needs only the
+    // cell's own right-hand side: taken here, with k_gs's arithmetic
+    const int cc = (int)lin(C.geo, I, J, K);
+    OpNb<T> nb;
+    neighbours(C, I, J, K, cc, nb);
+    const T z[3] = {T(0), T(0), T(0)};
+    C.x[cc] = gs_formula(C.geo, C.w, C.b[cc], nb.blo, nb.bhi, z, z);
+  }
 }
 
+// sweep: also take the coarse level's first Gauss-Seidel sweep from x = 0
 template <typename T>
-void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s) {
+void launch_residual_restrict(const MGLevel<T>& F, const MGLevel<T>& C, cudaStream_t s, bool sweep) {
   const dim3 bs(32, 4, 2);
   const dim3 gs((C.geo.n[0] + 31) / 32, (C.geo.n[1] + 3) / 4, (C.geo.n[2] + 1) / 2);
-  k_residual_restrict<T><<<gs, bs, 0, s>>>(F, C);
+  k_residual_restrict<T><<<gs, bs, 0, s>>>(F, C, sweep ? 1 : 0);
 }
 
 // the coarsening factor of an axis is 1 or 2
@@ -781,8 +791,7 @@ void launch_ctl_store(const SolveCtl* ctl, SolveCtl* rec, int* sticky, cudaStrea
                                     cudaStream_t);                                           \
   template void launch_zero<T>(T*, long long, cudaStream_t);                                 \
   template void launch_gs<T>(const MGLevel<T>&, int, cudaStream_t);                          \
-  template void launch_residual_restrict<T>(const MGLevel<T>&, const MGLevel<T>&,            \
-                                            cudaStream_t);                                   \
+  template void launch_residual_restrict<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t, bool); \
   template void launch_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);       \
   template void launch_gs_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, int, cudaStream_t); \
   template void launch_gs_zero<T>(const MGLevel<T>&, int, cudaStream_t);                      \
