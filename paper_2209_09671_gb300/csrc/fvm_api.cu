@@ -608,8 +608,14 @@ void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, 
   // of the first cycle, the addition on the last sweep of the last one
   const int m = c->prm.mx_inner_cycles;
   const int start0 = residual_takes_first_sweep(c) ? kStartFirstSwept : kStartZero;
+  // a cycle after the first begins with a colour-0 sweep right after the
+  // previous cycle's last one, also of colour 0, on the same right-hand side
+  // with the other colour unchanged: it would write the same values again,
+  // so it is skipped (when both smoothing steps sweep on the finest level)
+  const int startq = c->prm.mg_pre > 0 && c->prm.mg_post > 0 && c->nlev > 1 ? kStartFirstSwept
+                                                                             : kStartAsIs;
   for (int q = 0; q < m; ++q)
-    vcycle<float>(c, Ls, 0, crtol, q == 0 ? start0 : kStartAsIs, q == m - 1 ? p : nullptr);
+    vcycle<float>(c, Ls, 0, crtol, q == 0 ? start0 : startq, q == m - 1 ? p : nullptr);
   (void)N;
   (void)s;
   mixed_residual(c, p, b, be);
