@@ -808,6 +808,8 @@ def run_ours(args, rank, world, local_rank):
         if alg_bytes_per_cell(k, True) is not None and k not in FP64_FLOPS_PER_CELL:
             hbm_top = roofline_of(k, *v)
             break
+    # the FP64-bound defect-correction residual against the measured FP64 FMA rate
+    fp64_res = roofline_of("residual64", *prof["residual64"]) if prof.get("residual64", (0,))[0] else None
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3),
                    "share": round(v[1] / 1e3 / prof_elapsed, 4)} for k, v in prof.items() if v[0]}
     n_outer = sum(info["vcycles"]) / 3.0
@@ -911,6 +913,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": f"inputs larger than L2 (state {N * 28 / 2**20:.0f} MiB)"},
         "roofline": roof,
         "roofline_top_hbm_kernel": hbm_top,
+        "roofline_residual64": fp64_res,
         "roofline_whole_step": whole,
         "fma_peaks_tflops": {"f64": fma64["tflops"], "f32": fma32["tflops"],
                              "how": "fvm_fma_peak: 8 independent FMA chains per thread, "
