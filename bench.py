@@ -61,7 +61,7 @@ def alg_bytes_per_cell(cls: str, mixed: bool) -> float | None:
         "smooth": 2 * s,
         "div_rhs": 3 * s + 8,
         "correct": 6 * s + 8 + s + 3 * s,        # u*, Sn u, p, alpha in; u out
-        "residual64": 8 + 8 + 4 + 4,             # p, b, alpha in; float r out
+        "residual64": 8 + 8 + 4 + 4 + 4,         # p, b, alpha in; float r and the first sweep's e out
         "add_correction": 8 + 4 + 8,
         "beta": s + 3 * s,
     }
@@ -79,7 +79,7 @@ def compulsory_bytes_per_cell(cls: str, mixed: bool) -> float | None:
         "gs_fused_post": 2 * s + s + 3 * s + s / 8,
         "restrict_fine": 2 * s + s + 3 * s + 2 * s / 8,
         "prolong_fine": 2 * s + s / 8,
-        "residual64": 8 + 8 + 3 * 4 + 4,         # p, b, float beta in; float r out
+        "residual64": 8 + 8 + 3 * 4 + 4 + 4,     # p, b, float beta in; float r, e out
         "correct": 6 * s + 8 + 3 * s + 3 * s,    # u*, Sn u, p, beta in; u out
         "beta": s + 3 * s,
     }
