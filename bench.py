@@ -113,6 +113,8 @@ def parse():
     ap.add_argument("--f64-steps", type=int, default=3, help="steps of the FP64 side measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--copy-streams", type=int, default=6, help="copy streams of the host-buffer measurement")
+    ap.add_argument("--copy-chunks", type=int, default=1, help="chunks per field of the host-buffer measurement")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the mixed-against-FP64 error report at 64^3")
     ap.add_argument("--channel-steps", type=int, default=20,
@@ -827,13 +829,35 @@ def run_ours(args, rank, world, local_rank):
         host = {k: v.to("cpu").pin_memory() for k, v in state.items()}
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         d2h = h2d
+        # the fields' copies cut into chunks spread over several copy streams, so
+        # that several copy engines run at once; the solver's stream waits for all
+        # of them before the step and they wait for the step before reading back
+        n_cs = args.copy_streams
+        cstreams = [torch.cuda.Stream(device=dev) for _ in range(n_cs)]
+        chunks = []
+        for k in state:
+            dflat, hflat = state[k].view(-1), host[k].view(-1)
+            step_c = -(-dflat.numel() // args.copy_chunks)
+            for a in range(0, dflat.numel(), step_c):
+                chunks.append((dflat[a:a + step_c], hflat[a:a + step_c]))
+
+        def copies(to_device):
+            for cs in cstreams:
+                cs.wait_stream(stream)
+            for q, (dv, hv) in enumerate(chunks):
+                with torch.cuda.stream(cstreams[q % n_cs]):
+                    if to_device:
+                        dv.copy_(hv, non_blocking=True)
+                    else:
+                        hv.copy_(dv, non_blocking=True)
+            for cs in cstreams:
+                stream.wait_stream(cs)
+
         with torch.cuda.stream(stream):
             for _ in range(2):
-                for k in state:
-                    state[k].copy_(host[k], non_blocking=True)
+                copies(True)
                 solver.fvm_step(state, step_idx, 0.0, info=False)
-                for k in state:
-                    host[k].copy_(state[k], non_blocking=True)
+                copies(False)
                 step_idx += 1
         stream.synchronize()
         e2e_steps = max(3, args.steps // 2)
@@ -843,11 +867,9 @@ def run_ours(args, rank, world, local_rank):
         e0.record(stream)
         with torch.cuda.stream(stream):
             for _ in range(e2e_steps):
-                for k in state:
-                    state[k].copy_(host[k], non_blocking=True)
+                copies(True)
                 solver.fvm_step(state, step_idx, 0.0, info=False)
-                for k in state:
-                    host[k].copy_(state[k], non_blocking=True)
+                copies(False)
                 step_idx += 1
         e1.record(stream)
         stream.synchronize()
