@@ -409,6 +409,8 @@ struct SweepFold {
   const MGLevel<T>* corr = nullptr;   // first sweep: the coarse correction of this level (prolongation)
   bool zero = false;                  // first sweep: x starts at 0 (zeroes the other colour)
   bool skip_first = false;            // first sweep: already taken (by k_residual64)
+  const int* gate = nullptr;          // first sweep: skipped on the device once *gate >= gate_min
+  int gate_min = 0;
   double* addp = nullptr;             // last sweep: p += x (the mixed form's float level 0)
 };
 
@@ -436,6 +438,8 @@ void smooth(fvm_ctx* c, MGLevel<T>& L, int l, int iters, int first,
       TIMED(c, kg, 1, launch_gs_zero<T>(L, colour, c->stream));
     else if (t == last && f.addp)
       addp_sweep(c, kg, L, colour, f.addp);
+    else if (t == 0 && f.gate)
+      TIMED(c, kg, 1, launch_gs<T>(L, colour, c->stream, f.gate, f.gate_min));
     else
       TIMED(c, kg, 1, launch_gs<T>(L, colour, c->stream));
   }
@@ -463,9 +467,18 @@ int tail_start(const fvm_ctx* c) {
 // V(pre, post) cycle: red-black sweeps before the coarse correction,
 // black-red after, CG on the coarsest level; the levels from tail_start()
 // down run in one kernel
-// How the finest level's x starts: as it is, at 0 (not yet zeroed), or with
-// the first sweep from 0 already taken by k_residual64 (mixed form).
-enum { kStartAsIs = 0, kStartZero = 1, kStartFirstSwept = 2 };
+// How the finest level's x starts: as it is, at 0 (not yet zeroed), with the
+// first sweep already taken (by k_residual64 in the mixed form, or skipped
+// because it would repeat the previous cycle's last sweep), or with that skip
+// decided on the device (FP64 solve graph: from the second cycle on).
+enum { kStartAsIs = 0, kStartZero = 1, kStartFirstSwept = 2, kStartGated = 3 };
+
+// a cycle's first finest-level sweep repeats the previous cycle's last one
+// (same colour, same right-hand side, the other colour unchanged) when both
+// smoothing steps sweep on a finest level of its own
+bool first_sweep_repeats(const fvm_ctx* c) {
+  return c->prm.mg_pre > 0 && c->prm.mg_post > 0 && c->nlev > 1;
+}
 
 // the mixed form's residual kernel takes the first sweep of each inner solve
 // when that solve begins with a sweep on a finest level of its own
@@ -516,6 +529,11 @@ void vcycle(fvm_ctx* c, MGLevel<T>* Ls, int l, double coarse_rtol, int start = k
     SweepFold<T> fpre;
     fpre.zero = fold_zero;
     fpre.skip_first = start == kStartFirstSwept;
+    if (start == kStartGated) {
+      // the controller counts the cycle being run: 1 in the first
+      fpre.gate = &c->ctl->iters;
+      fpre.gate_min = 2;
+    }
     smooth<T>(c, Ls[l], l, pre, 0, fpre);
     // the next level's first sweep rides on the restriction when that level
     // sweeps on its own (not the tail, not the coarsest)
@@ -563,7 +581,9 @@ fvm_status solve_f64(fvm_ctx* c, double* p, double* b, int* cycles_out, double* 
   }
   const int fixed = c->prm.mg_fixed_cycles;
   if (fixed > 0) {
-    for (int q = 0; q < fixed; ++q) vcycle<double>(c, Ls, 0, c->prm.coarse_rtol);
+    const int later = first_sweep_repeats(c) ? kStartFirstSwept : kStartAsIs;
+    for (int q = 0; q < fixed; ++q)
+      vcycle<double>(c, Ls, 0, c->prm.coarse_rtol, q == 0 ? kStartAsIs : later);
     cycles = fixed;
     if (want_rel) {
       double r2;
@@ -581,7 +601,8 @@ fvm_status solve_f64(fvm_ctx* c, double* p, double* b, int* cycles_out, double* 
       rel = sqrt(r2) / bn;
       if (!isfinite(rel)) return set_err(c, FVM_EUNSTABLE, "non-finite pressure residual");
       if (rel <= c->prm.mg_rtol || cycles >= c->prm.mg_max_cycles) break;
-      vcycle<double>(c, Ls, 0, c->prm.coarse_rtol);
+      vcycle<double>(c, Ls, 0, c->prm.coarse_rtol,
+                     cycles > 0 && first_sweep_repeats(c) ? kStartFirstSwept : kStartAsIs);
       ++cycles;
     }
   }
@@ -612,8 +633,7 @@ void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, 
   // previous cycle's last one, also of colour 0, on the same right-hand side
   // with the other colour unchanged: it would write the same values again,
   // so it is skipped (when both smoothing steps sweep on the finest level)
-  const int startq = c->prm.mg_pre > 0 && c->prm.mg_post > 0 && c->nlev > 1 ? kStartFirstSwept
-                                                                             : kStartAsIs;
+  const int startq = first_sweep_repeats(c) ? kStartFirstSwept : kStartAsIs;
   for (int q = 0; q < m; ++q)
     vcycle<float>(c, Ls, 0, crtol, q == 0 ? start0 : startq, q == m - 1 ? p : nullptr);
   (void)N;
@@ -724,7 +744,8 @@ void graph_body(fvm_ctx* c, double* p, cudaGraphConditionalHandle h) {
     MGLevel<double> Ls[kMaxLevels];
     double* be[3] = {(double*)c->beta0[0], (double*)c->beta0[1], (double*)c->beta0[2]};
     hierarchy<double>(c, p, c->b, be, Ls);
-    vcycle<double>(c, Ls, 0, c->prm.coarse_rtol);
+    vcycle<double>(c, Ls, 0, c->prm.coarse_rtol,
+                   first_sweep_repeats(c) ? kStartGated : kStartAsIs);
     TIMED(c, FVM_K_RESNORM, 2, launch_residual_norm2<double>(Ls[0], c->partial, c->scal + 1, s));
   }
   TIMED(c, FVM_K_MISC, 1,

@@ -136,8 +136,10 @@ void launch_sub_mean(double* a, long long n, const double* sum, cudaStream_t s);
 template <typename T>
 void launch_zero(T* a, long long n, cudaStream_t s);
 
+// gate (optional): the sweep does nothing once *gate >= gate_min
 template <typename T>
-void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s);
+void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s, const int* gate = nullptr,
+               int gate_min = 0);
 
 
 template <typename T>

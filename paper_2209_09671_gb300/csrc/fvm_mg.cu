@@ -190,8 +190,12 @@ __device__ __forceinline__ void gs_point(const MGLevel<T>& L, int i, int j, int 
   L.x[c] = gs_formula(g, L.w, L.b[c], nb.blo, nb.bhi, xlo, xhi);
 }
 
+// gate (optional): the sweep does nothing once *gate >= gate_min (the FP64
+// solve graph skips the first sweep of every cycle after the first, which
+// would repeat the previous cycle's last sweep)
 template <typename T>
-__global__ void k_gs(MGLevel<T> L, int colour) {
+__global__ void k_gs(MGLevel<T> L, int colour, const int* __restrict__ gate, int gate_min) {
+  if (gate && *gate >= gate_min) return;
   const Geo& g = L.geo;
   const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -203,11 +207,11 @@ __global__ void k_gs(MGLevel<T> L, int colour) {
 }
 
 template <typename T>
-void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s) {
+void launch_gs(const MGLevel<T>& L, int colour, cudaStream_t s, const int* gate, int gate_min) {
   const int hx = (L.geo.n[0] + 1) / 2;
   dim3 bs(32, 4, 2);
   dim3 gs((hx + 31) / 32, (L.geo.n[1] + 3) / 4, (L.geo.n[2] + 1) / 2);
-  k_gs<T><<<gs, bs, 0, s>>>(L, colour);
+  k_gs<T><<<gs, bs, 0, s>>>(L, colour, gate, gate_min);
 }
 
 // coarse b = mean over children of (b - L x) on the fine level; coarse x = 0
@@ -790,7 +794,7 @@ void launch_ctl_store(const SolveCtl* ctl, SolveCtl* rec, int* sticky, cudaStrea
   template void launch_sum_field<T>(const T*, long long, bool, double*, double*,             \
                                     cudaStream_t);                                           \
   template void launch_zero<T>(T*, long long, cudaStream_t);                                 \
-  template void launch_gs<T>(const MGLevel<T>&, int, cudaStream_t);                          \
+  template void launch_gs<T>(const MGLevel<T>&, int, cudaStream_t, const int*, int);        \
   template void launch_residual_restrict<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t, bool); \
   template void launch_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, cudaStream_t);       \
   template void launch_gs_prolong<T>(const MGLevel<T>&, const MGLevel<T>&, int, cudaStream_t); \

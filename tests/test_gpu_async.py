@@ -44,8 +44,13 @@ def test_graph_solve_equals_host_loop(precision):
         assert x["rel_residual"] == y["rel_residual"]
         assert x["dt"] == y["dt"]
     # the graph adds per solve a controller reset, a test before the loop,
-    # one test per cycle, the zero-rhs guard and the record store
+    # one test per cycle, the zero-rhs guard and the record store; in FP64 it
+    # also launches every cycle's first finest-level sweep, which from the
+    # second cycle on does nothing on the device (it would repeat the previous
+    # cycle's last sweep), where the host loop does not launch it
     extra = sum(4 + c for info in ia for c in info["vcycles"])
+    if precision == cases.F64:
+        extra += sum(max(c - 1, 0) for info in ia for c in info["vcycles"])
     assert na == nb + extra
 
 
