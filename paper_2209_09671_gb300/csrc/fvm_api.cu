@@ -623,10 +623,9 @@ fvm_status solve_f64(fvm_ctx* c, double* p, double* b, int* cycles_out, double* 
 // norm.
 void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, double* b,
                  float* const* be, double crtol) {
-  cudaStream_t s = c->stream;
-  const long long N = c->g.N;
   // e = 0, the inner cycles and p += e: the zeroing rides on the first sweep
-  // of the first cycle, the addition on the last sweep of the last one
+  // of the first cycle (or that sweep was taken by the residual kernel), the
+  // addition on the last sweep of the last one
   const int m = c->prm.mx_inner_cycles;
   const int start0 = residual_takes_first_sweep(c) ? kStartFirstSwept : kStartZero;
   // a cycle after the first begins with a colour-0 sweep right after the
@@ -636,8 +635,6 @@ void refine_once(fvm_ctx* c, MGLevel<float>* Ls, const float* alpha, double* p, 
   const int startq = first_sweep_repeats(c) ? kStartFirstSwept : kStartAsIs;
   for (int q = 0; q < m; ++q)
     vcycle<float>(c, Ls, 0, crtol, q == 0 ? start0 : startq, q == m - 1 ? p : nullptr);
-  (void)N;
-  (void)s;
   mixed_residual(c, p, b, be);
 }
 
