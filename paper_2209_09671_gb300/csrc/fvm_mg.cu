@@ -600,16 +600,57 @@ __device__ void tail_body(const MGLevel<T>* Ls, int nl, double* r, double* d, do
   }
 }
 
+// staged: the tail levels' x, b and betas are copied into dynamic shared
+// memory first (x and b of the top level, the betas of every level; the
+// lower levels' x and b are set by the restrictions inside the tail), the
+// tail runs on those copies, and the top level's x is copied back for the
+// prolongation.  The arithmetic is the same as on the global arrays; only the
+// latency of each sweep's loads changes.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A) {
+__global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A, int staged) {
   __shared__ double sh[33];
   __shared__ CgSmem cs;
-  tail_body(A.L, A.nl, A.r, A.d, A.Ad, A.rtol, A.maxit, A.pre, A.post, sh, cs);
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  if (!staged) {
+    tail_body(A.L, A.nl, A.r, A.d, A.Ad, A.rtol, A.maxit, A.pre, A.post, sh, cs);
+    return;
+  }
+  MGLevel<T> L[kTailLevels];
+  T* base = reinterpret_cast<T*>(tail_smem);
+  for (int q = 0; q < A.nl; ++q) {
+    L[q] = A.L[q];
+    const int n = (int)L[q].geo.N;
+    L[q].x = base;
+    L[q].b = base + n;
+    for (int d = 0; d < 3; ++d) L[q].beta[d] = base + (2 + d) * n;
+    base += 5 * n;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      for (int d = 0; d < 3; ++d) L[q].beta[d][c] = A.L[q].beta[d][c];
+      if (q == 0) {
+        L[0].x[c] = A.L[0].x[c];
+        L[0].b[c] = A.L[0].b[c];
+      }
+    }
+  }
+  __syncthreads();
+  tail_body(L, A.nl, A.r, A.d, A.Ad, A.rtol, A.maxit, A.pre, A.post, sh, cs);
+  __syncthreads();
+  for (int c = threadIdx.x; c < (int)L[0].geo.N; c += blockDim.x) A.L[0].x[c] = L[0].x[c];
 }
 
 template <typename T>
 void launch_coarse_tail(const TailArgs<T>& A, cudaStream_t s) {
-  k_coarse_tail<T><<<1, 1024, 0, s>>>(A);
+  // stage the levels of the FP64 form when they fit beside the kernel's
+  // static shared memory (256^3 melt pool: tail 14.0 -> 9.5 ms per FP64 step;
+  // the float tail was slower staged, 112 -> 124 us per call, and reads the
+  // global arrays)
+  size_t bytes = 0;
+  for (int q = 0; q < A.nl; ++q) bytes += 5 * (size_t)A.L[q].geo.N * sizeof(T);
+  const size_t limit = 227 * 1024 - sizeof(CgSmem) - 33 * sizeof(double) - 1024;
+  const bool staged = sizeof(T) == sizeof(double) && bytes <= limit;
+  if (staged)
+    cudaFuncSetAttribute(k_coarse_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k_coarse_tail<T><<<1, 1024, staged ? bytes : 0, s>>>(A, staged ? 1 : 0);
 }
 
 template <typename T>
