@@ -641,9 +641,8 @@ __global__ void __launch_bounds__(1024) k_coarse_tail(TailArgs<T> A, int staged)
 template <typename T>
 void launch_coarse_tail(const TailArgs<T>& A, cudaStream_t s) {
   // stage the levels of the FP64 form when they fit beside the kernel's
-  // static shared memory (256^3 melt pool: tail 14.0 -> 9.5 ms per FP64 step;
-  // the float tail was slower staged, 112 -> 124 us per call, and reads the
-  // global arrays)
+  // static shared memory (the float tail was slower staged, 112 -> 124 us per
+  // call at 256^3, and reads the global arrays)
   size_t bytes = 0;
   for (int q = 0; q < A.nl; ++q) bytes += 5 * (size_t)A.L[q].geo.N * sizeof(T);
   const size_t limit = 227 * 1024 - sizeof(CgSmem) - 33 * sizeof(double) - 1024;
